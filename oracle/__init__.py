@@ -1,0 +1,26 @@
+"""FP64 CPU oracle of the fast broadband beamspace transform.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by the CPU-baseline
+leg of bench.py. The CUDA library and its Python binding never import it.
+
+Parity status of each function is stated in fbst_oracle's docstrings; every function is pinned by
+the tests in tests/test_oracle_pins.py except the size of the noise-free bias of a plane wave,
+which the paper gives no number for ("parity unpinned": only a sanity bound is checked).
+"""
+from .fbst_oracle import (  # noqa: F401
+    Problem,
+    Stage2Factors,
+    make_problem,
+    F_theta,
+    F_u,
+    stage1_time,
+    stage1_space,
+    fan_coefficients,
+    gram,
+    fbst,
+    dense_operator,
+    lstsq_augmented,
+    noise_power_trace,
+    delay_and_sum_exact,
+    rel_l2,
+)

@@ -1,0 +1,282 @@
+"""Plain FP64 CPU oracle of the fast broadband beamspace transform (FBST).
+
+TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's CPU-baseline
+leg may import this module. The product path (the CUDA library and its Python binding) never
+calls it, and it shares no code, tables or constants with that path.
+
+What it computes. The FBST reaches exactly (up to rounding) the regularised least-squares beam
+of Sec. III-A: for each beam b,
+
+    w_b     = F_b^H y                               (Eq. (5), the fan of Sec. IV computes it)
+    beta_b  = (F_b^H F_b + delta I)^{-1} w_b        (Eq. (5); Sec. V solves it fast)
+    bhat_b  = F_u beta_b                            (Eq. (7))
+
+with F_b the MN x L non-uniform Fourier matrix of Eq. (6) and F_u the N x L reconstruction
+matrix of Eq. (7). So the oracle is that definition written out in float64 numpy:
+
+* w_b by direct (non-FFT) sums, ordered as in Sec. IV: a direct sum over time for every sensor,
+  then a direct sum over sensors for every frequency index (Eq. (9)-(12)).
+* A_b = F_b^H F_b + delta I by direct sums. F_b factors as (carrier phase of the sensor) x
+  (time part) x (delay part), so its Gram matrix is the elementwise product of the Gram matrix of
+  the time part and that of the delay part; both are plain matrix products. No closed form and no
+  Toeplitz shortcut is used.
+* beta_b by dense LU (scipy.linalg.lu_factor / lu_solve), bhat_b by a dense product with F_u.
+
+Conventions (0-based everywhere, units of samples, so T_s = 1):
+* n = 0..N-1 (t_n = n), sensors m = 0..M-1 with positions p_m from synth.array_positions.
+* ell = 0..L-1 stands for the paper's ell = 1..L, so ell' = (ell + 1) - L/2 (Eq. (3) and Eq. (12)).
+* omega_ell * T_s = 2*pi*eps*ell'/L (Eq. (3)).
+* Beams: u_b = -1 + 2b/B for a linear array; for an mx-by-my rectangular array b = a*by + c with
+  (u_a, v_c) = (-1 + 2a/bx, -1 + 2c/by). (Eq. (11) is garbled for even B; this grid covers [-1, 1).)
+* fb = 2*Omega/f_c, rho = fb/(2+fb), f_c*T_s = 1/fb and tau_{b,m} = rho*(u_b*px_m + v_b*py_m)
+  (Sec. IV for the linear array, App. B for the planar array).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from functools import cached_property
+
+import numpy as np
+import scipy.linalg
+
+from synth.planewave import ArrayGeometry, array_positions
+
+TWO_PI_J = 2j * np.pi
+
+
+@dataclass(frozen=True)
+class Problem:
+    """One FBST problem: array, beam grid, block length and basis parameters."""
+
+    geom: ArrayGeometry
+    bx: int
+    by: int
+    N: int
+    L: int
+    frac_bw: float
+    epsilon: float
+    delta: float  # absolute regulariser delta of Eq. (5)
+
+    @property
+    def M(self) -> int:
+        return self.geom.M
+
+    @property
+    def B(self) -> int:
+        return self.bx * self.by
+
+    @property
+    def rho(self) -> float:
+        return self.frac_bw / (2.0 + self.frac_bw)
+
+    @cached_property
+    def positions(self) -> np.ndarray:
+        return array_positions(self.geom)
+
+    @cached_property
+    def directions(self) -> np.ndarray:
+        """(B, 2) direction cosines of the beam grid."""
+        if self.geom.kind == "ula":
+            u = -1.0 + 2.0 * np.arange(self.bx) / self.bx
+            return np.stack([u, np.zeros_like(u)], axis=1)
+        a, c = np.meshgrid(np.arange(self.bx), np.arange(self.by), indexing="ij")
+        return np.stack([-1.0 + 2.0 * a.ravel() / self.bx, -1.0 + 2.0 * c.ravel() / self.by], axis=1)
+
+    @cached_property
+    def lprime(self) -> np.ndarray:
+        """ell' = ell - L/2 for the paper's ell = 1..L (Eq. (3))."""
+        return np.arange(1, self.L + 1, dtype=np.float64) - self.L / 2
+
+    def tau(self, beams=None) -> np.ndarray:
+        """tau_{b,m}/T_s = rho*(u_b*px_m + v_b*py_m), shape (len(beams), M)."""
+        d = self.directions if beams is None else self.directions[np.asarray(beams)]
+        return self.rho * (d @ self.positions.T)
+
+
+def make_problem(kind: str, mx: int, my: int, bx: int, by: int, N: int, frac_bw: float,
+                 epsilon: float = 1.01, gamma: float = 2.0, delta: float | None = None,
+                 delta_rel: float | None = None, L: int | None = None) -> Problem:
+    """Build a Problem. L = gamma*N unless given. delta is absolute, or delta_rel*M*N."""
+    geom = ArrayGeometry(kind, mx, my)
+    if L is None:
+        L = int(round(gamma * N))
+    if delta is None:
+        delta = float(delta_rel) * (geom.M * N)
+    return Problem(geom, bx, by, N, L, float(frac_bw), float(epsilon), float(delta))
+
+
+# ----------------------------------------------------------------------------------------------
+# Explicit matrices (Eq. (6) and Eq. (7)) -- used directly on small problems and as pins.
+# ----------------------------------------------------------------------------------------------
+
+def F_theta(pb: Problem, b: int) -> np.ndarray:
+    """The MN x L matrix of Eq. (6) for beam b; row m*N + n is (sensor m, snapshot n).
+
+    [F]_{(m,n), ell} = exp(-2j*pi*f_c*tau_m) * exp(j*omega_ell*(t_n - tau_m)).
+    """
+    tau = pb.tau([b])[0]                      # (M,)
+    n = np.arange(pb.N, dtype=np.float64)
+    t_minus_tau = n[None, :] - tau[:, None]   # (M, N)
+    carrier = np.exp(-TWO_PI_J * tau / pb.frac_bw)[:, None, None]
+    basis = np.exp(TWO_PI_J * pb.epsilon * np.multiply.outer(t_minus_tau, pb.lprime) / pb.L)
+    return (carrier * basis).reshape(pb.M * pb.N, pb.L)
+
+
+def F_u(pb: Problem) -> np.ndarray:
+    """[F_u]_{n, ell} = exp(j*omega_ell*t_n) (Eq. (7)), shape (N, L)."""
+    n = np.arange(pb.N, dtype=np.float64)
+    return np.exp(TWO_PI_J * pb.epsilon * np.multiply.outer(n, pb.lprime) / pb.L)
+
+
+# ----------------------------------------------------------------------------------------------
+# Stage 1: w_b = F_b^H y by direct sums (Sec. IV, Eq. (9)-(12); App. B for the planar array)
+# ----------------------------------------------------------------------------------------------
+
+def stage1_time(pb: Problem, y: np.ndarray) -> np.ndarray:
+    """yhat[..., m, ell] = sum_n y[..., m, n] exp(-2j*pi*eps*ell'*n/L)  (the first sum of Sec. IV).
+
+    y has shape (..., M, N); the result has shape (..., M, L), complex128.
+    """
+    n = np.arange(pb.N, dtype=np.float64)
+    E = np.exp(-TWO_PI_J * pb.epsilon * np.multiply.outer(n, pb.lprime) / pb.L)  # (N, L)
+    return np.asarray(y, dtype=np.complex128) @ E
+
+
+def stage1_space(pb: Problem, yhat: np.ndarray, beams=None, chunk: int = 64) -> np.ndarray:
+    """w[..., b, ell] = sum_m yhat[..., m, ell] exp(2j*pi*(1/fb + eps*ell'/L)*tau_{b,m}).
+
+    This is the second sum of Sec. IV (and the two array sums of App. B written as one sum over
+    the elements). yhat has shape (..., M, L); the result has shape (..., nbeams, L).
+    """
+    yhat = np.asarray(yhat, dtype=np.complex128)
+    tau = pb.tau(beams)                                   # (nb, M)
+    lead = yhat.shape[:-2]
+    Y = yhat.reshape((-1,) + yhat.shape[-2:])             # (K, M, L)
+    out = np.empty((Y.shape[0], tau.shape[0], pb.L), dtype=np.complex128)
+    for l0 in range(0, pb.L, chunk):
+        lp = pb.lprime[l0:l0 + chunk]
+        kappa = 1.0 / pb.frac_bw + pb.epsilon * lp / pb.L           # (c,)
+        S = np.exp(TWO_PI_J * kappa[:, None, None] * tau[None, :, :])  # (c, nb, M)
+        # out[k, b, l] = sum_m S[l, b, m] * Y[k, m, l]
+        out[:, :, l0:l0 + lp.size] = np.einsum("lbm,kml->kbl", S, Y[:, :, l0:l0 + lp.size], optimize=True)
+    return out.reshape(lead + (tau.shape[0], pb.L))
+
+
+def fan_coefficients(pb: Problem, y: np.ndarray, beams=None) -> np.ndarray:
+    """w = F_b^H y for every beam: (..., M, N) -> (..., nbeams, L)."""
+    return stage1_space(pb, stage1_time(pb, y), beams)
+
+
+# ----------------------------------------------------------------------------------------------
+# Stage 2: beta_b = (F_b^H F_b + delta I)^{-1} w_b, bhat_b = F_u beta_b (Eq. (5), Eq. (7), Sec. V)
+# ----------------------------------------------------------------------------------------------
+
+def gram(pb: Problem, b: int) -> np.ndarray:
+    """A_b = F_b^H F_b + delta I by direct sums (Eq. (5); its entries are those of Sec. V).
+
+    With E[n, ell] = exp(j*omega_ell*t_n) and phi[ell, m] = exp(-j*omega_ell*tau_m), the entry
+    [F_b]_{(m,n),ell} is carrier_m * E[n,ell] * phi[ell,m], so
+    [F_b^H F_b]_{ell,k} = (sum_n conj(E[n,ell]) E[n,k]) * (sum_m conj(phi[ell,m]) phi[k,m]):
+    the elementwise product of two Gram matrices (the unit-modulus carrier drops out).
+    """
+    E = F_u(pb)                                                                  # (N, L)
+    tau = pb.tau([b])[0]
+    phi = np.exp(-TWO_PI_J * pb.epsilon * np.multiply.outer(pb.lprime, tau) / pb.L)  # (L, M)
+    A = (E.conj().T @ E) * (phi.conj() @ phi.T)
+    A[np.diag_indices(pb.L)] += pb.delta
+    return A
+
+
+class Stage2Factors:
+    """LU factors of every requested A_b, built once (the per-plan part of the oracle)."""
+
+    def __init__(self, pb: Problem, beams=None):
+        self.pb = pb
+        self.beams = np.arange(pb.B) if beams is None else np.asarray(beams)
+        self.Fu = F_u(pb)
+        self.lu = [scipy.linalg.lu_factor(gram(pb, int(b))) for b in self.beams]
+
+    def apply(self, w: np.ndarray) -> np.ndarray:
+        """w: (nblk, nbeams, L) in the order of self.beams -> bhat: (nblk, nbeams, N)."""
+        w = np.asarray(w, dtype=np.complex128)
+        out = np.empty(w.shape[:-1] + (self.pb.N,), dtype=np.complex128)
+        for i, lu in enumerate(self.lu):
+            beta = scipy.linalg.lu_solve(lu, w[:, i, :].T)      # (L, nblk)
+            out[:, i, :] = (self.Fu @ beta).T
+        return out
+
+    def coefficients(self, w: np.ndarray) -> np.ndarray:
+        """beta = A_b^{-1} w_b for every requested beam, shape (nblk, nbeams, L)."""
+        w = np.asarray(w, dtype=np.complex128)
+        out = np.empty_like(w)
+        for i, lu in enumerate(self.lu):
+            out[:, i, :] = scipy.linalg.lu_solve(lu, w[:, i, :].T).T
+        return out
+
+
+def fbst(pb: Problem, y: np.ndarray, beams=None, factors: Stage2Factors | None = None) -> np.ndarray:
+    """Full FBST: y (nblk, M, N) -> bhat (nblk, nbeams, N), complex128."""
+    y = np.asarray(y)
+    if y.ndim == 2:
+        y = y[None]
+    if factors is None:
+        factors = Stage2Factors(pb, beams)
+    w = fan_coefficients(pb, y, factors.beams)
+    return factors.apply(w)
+
+
+def dense_operator(pb: Problem, b: int) -> np.ndarray:
+    """G_b = F_u A_b^{-1} (N x L), the precomputed operator of Sec. III-B / Sec. V."""
+    A = gram(pb, b)
+    # G_b = F_u A^{-1}  <=>  G_b^T = A^{-T} F_u^T, and A^T = conj(A) for Hermitian A.
+    return scipy.linalg.solve(A.T, F_u(pb).T).T
+
+
+# ----------------------------------------------------------------------------------------------
+# Tools used by the pins (not part of the method)
+# ----------------------------------------------------------------------------------------------
+
+def lstsq_augmented(F: np.ndarray, y: np.ndarray, delta: float) -> np.ndarray:
+    """argmin ||F beta - y||^2 + delta ||beta||^2 by QR least squares on [F; sqrt(delta) I]."""
+    L = F.shape[1]
+    Fa = np.vstack([F, np.sqrt(delta) * np.eye(L)])
+    ya = np.concatenate([y, np.zeros(L, dtype=np.complex128)])
+    return np.linalg.lstsq(Fa, ya, rcond=None)[0]
+
+
+def noise_power_trace(pb: Problem, b: int) -> float:
+    """sigma^-2 E||F_u A^{-1} F^H n||^2 = tr(F_u A^{-1} F^H F A^{-1} F_u^H) for white noise n.
+
+    The discrete analogue of the variance expression of Sec. VII (the paper integrates r(t,t)
+    over [0, T]; here the beam is read at the N sample times instead).
+    """
+    F = F_theta(pb, b)
+    A = gram(pb, b)
+    K = np.linalg.solve(A, F.conj().T)          # A^{-1} F^H  (L x MN)
+    Op = F_u(pb) @ K                            # N x MN
+    return float(np.real(np.vdot(Op, Op)))
+
+
+def delay_and_sum_exact(record: np.ndarray, positions: np.ndarray, u: float, v: float,
+                        frac_bw: float, n_out: np.ndarray) -> np.ndarray:
+    """Delay-and-sum with exact (full-record) sinc fractional delays (Sec. III, before Eq. (2)).
+
+    b(t_n) = (1/M) sum_m exp(2j*pi*f_c*tau_m) y_m(t_n + tau_m), with y_m(t) rebuilt from all of
+    its samples by the sinc series y_m(t) = sum_k y_m[k] sinc(t - k). record: (M, n_total).
+    """
+    rho = frac_bw / (2.0 + frac_bw)
+    tau = rho * (u * positions[:, 0] + v * positions[:, 1])
+    k = np.arange(record.shape[1], dtype=np.float64)
+    out = np.zeros(len(n_out), dtype=np.complex128)
+    for m in range(record.shape[0]):
+        t = np.asarray(n_out, dtype=np.float64) + tau[m]
+        interp = np.sinc(np.subtract.outer(t, k)) @ record[m]
+        out += np.exp(TWO_PI_J * tau[m] / frac_bw) * interp
+    return out / record.shape[0]
+
+
+def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
+    """||a - b||_2 / ||b||_2 over all entries."""
+    a = np.asarray(a, dtype=np.complex128).ravel()
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
