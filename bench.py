@@ -1,0 +1,378 @@
+"""Benchmark of the FBST hot path on GB300.
+
+Default workload (C2): 256-element linear array, fb = 0.5, N = 256 snapshots per block, B = 256
+beams, L = 512, 64 contiguous blocks of one record per step, complex64 in and out, FP32 maths,
+Gohberg-Semencul stage 2. One step = fbst_execute over the 64 blocks (all three kernels).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 gs|dense_fp32]
+
+With N > 1 (torchrun) every rank runs its own replica of the plan on its own 64 blocks (weak
+scaling; the method has no cross-block exchange, so there is no collective on the data path).
+Rank 0 prints one JSON line. `value` is device time measured with CUDA events on the launching
+stream, L2 flushed (256 MiB write) before every timed step; `e2e` goes through the C-ABI host-buffer
+entry point with pinned host memory, copies included; `roofline` times each kernel live with
+events around its own C-ABI stage call; `cpu_baseline` times the FP64 oracle on the host cores
+on a bounded sample. `--impl reference` times the oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "beam-samples/s at rel err ≤1e-5 vs FP64 oracle, %HBM roofline; p50/p99 latency"
+UNIT = "beam-samples/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+SMS, FP32_LANES = 152, 128
+
+
+def load_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def fft_flops(P: int) -> float:
+    """Nominal complex FFT cost, 5 P log2 P."""
+    return 5.0 * P * math.log2(P)
+
+
+def flop_model(info) -> dict:
+    """Nominal FLOPs per launch unit of each kernel (5 P log2 P per transform, 6 per complex multiply,
+    2 per complex add), counted for the transforms the kernels perform."""
+    M, N, B, L = info.M, info.N, info.B, info.L
+    S, Pt = info.S_time, info.P_time
+    time_per_sensor = (1 + S) * fft_flops(Pt) + 6.0 * (N + S * Pt + L)
+    Ps = info.P_space_x
+    space_per_freq = 2 * fft_flops(Ps) + 6.0 * (M + Ps + B)
+    Pg, Pr, Sr = info.P_gs, info.P_rec, info.S_rec
+    gs = 6 * fft_flops(Pg) + 6.0 * 4 * Pg + 2.0 * Pg
+    rec = (Sr + 1) * fft_flops(Pr) + 6.0 * (L + Sr * Pr + N) + 2.0 * (Sr - 1) * Pr
+    return {"czt_time": time_per_sensor * M, "czt_space": space_per_freq * L, "stage2_gs": (gs + rec) * B}
+
+
+def alg_bytes(info) -> dict:
+    """Compulsory HBM bytes per block of each kernel (complex64 in + out, tables excluded)."""
+    M, N, B, L = info.M, info.N, info.B, info.L
+    return {"czt_time": 8.0 * (M * N + L * M), "czt_space": 8.0 * (L * M + B * L),
+            "stage2_gs": 8.0 * (B * L + B * N)}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(args):
+    from synth import configs
+    if args.workload == "C2":
+        nb = args.nblk or configs.CONFIGS["C2"]["nblk"]
+        return dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, nblk=nb, name="C2"), \
+            lambda: configs.config_data("C2", nblk=nb)["y"]
+    if args.workload == "ULA1024":
+        # Large linear array (the paper's scaling regime): M = B = 1024, N = 512, fb = 0.5.
+        def gen():
+            from synth.planewave import ula_config
+            return ula_config(1024, 512, args.nblk or 16, 0.5, 8, 10.0, 2024, Q=64)["y"]
+        return dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, nblk=args.nblk or 16,
+                    name="ULA1024"), gen
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def oracle_sample(w: dict, y: np.ndarray, beams, nblk: int, budget_s: float):
+    """Time the FP64 oracle (execute part, per-plan LU excluded) on a bounded sample."""
+    import oracle as O
+    pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], w["N"], frac_bw=w["frac_bw"],
+                        epsilon=1.01, delta_rel=1e-3)
+    t0 = time.perf_counter()
+    fac = O.Stage2Factors(pb, beams)
+    t_plan = time.perf_counter() - t0
+    done, t_exec = 0, 0.0
+    out = None
+    while t_exec < budget_s or done == 0:
+        t0 = time.perf_counter()
+        out = O.fbst(pb, y[:nblk], factors=fac)
+        t_exec += time.perf_counter() - t0
+        done += 1
+    samples = done * nblk * len(beams) * w["N"]
+    return samples / t_exec, t_plan, done, out, pb
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, gen = workload(args)
+    y = gen()
+    beams = np.linspace(0, w["bx"] * w["by"] - 1, 16).astype(int)
+    import oracle as O
+    pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], w["N"], frac_bw=w["frac_bw"],
+                        epsilon=1.01, delta_rel=1e-3)
+    fac = O.Stage2Factors(pb, beams)
+    for _ in range(args.warmup):
+        O.fbst(pb, y[:1], factors=fac)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.fbst(pb, y[:1], factors=fac)
+        times.append(time.perf_counter() - t0)
+    per_step = len(beams) * w["N"]
+    value = per_step * len(times) / sum(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{w['name']} oracle sample", "M": w["mx"] * w["my"],
+                                            "N": w["N"], "B": w["bx"] * w["by"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: 1 block x {len(beams)} beams of {w['name']} (FP64 numpy oracle, "
+                                       "per-plan LU excluded)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fbst", choices=["fbst", "reference"])
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--nblk", type=int, default=None)
+    ap.add_argument("--stage2", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build()
+    if dist is not None:
+        dist.barrier()
+    build()
+
+    w, gen = workload(args)
+    y_np = gen()
+    nblk = w["nblk"]
+    M, B, N = w["mx"] * w["my"], w["bx"] * w["by"], w["N"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    plan = fb.Plan(fb.make_geometry(w["kind"], w["mx"], w["my"], w["bx"], w["by"]), N,
+                   fb.make_band(w["frac_bw"], stage2=args.stage2, max_blocks=nblk))
+    info = plan.info
+    y = torch.from_numpy(y_np).to(dev)
+    out = torch.empty((nblk, B, N), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # Accuracy on a sample of beams (rank 0; untimed).
+    plan.execute(y, out, nblk)
+    torch.cuda.synchronize()
+    rel_err = None
+    if rank == 0:
+        import oracle as O
+        beams = np.array([0, 77, 128, B - 1])
+        pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], N, frac_bw=info.fb_num / info.fb_den,
+                            epsilon=info.eps_num / info.eps_den, delta=info.delta, L=info.L)
+        ref = O.fbst(pb, y_np[:2], beams=beams)
+        rel_err = O.rel_l2(out[:2].cpu().numpy()[:, beams], ref)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.execute(y, out, nblk)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plan.execute(y, out, nblk)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = float(nblk) * B * N * world
+    value = units * args.steps / (total_ms / 1e3)
+
+    # Per-kernel live timing: each kernel through its own C-ABI stage call, events on its stream.
+    kin = min(args.steps, 200)
+    yhat = torch.empty((nblk, info.L, M), dtype=torch.complex64, device=dev)
+    wbuf = torch.empty((nblk, B, info.L), dtype=torch.complex64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kin)]
+    for i in range(kin):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.czt_time(y, yhat, nblk)
+        ev[i][1].record(stream)
+        plan.czt_space(yhat, wbuf, nblk)
+        ev[i][2].record(stream)
+        plan.toeplitz_apply(wbuf, out, nblk)
+        ev[i][3].record(stream)
+    torch.cuda.synchronize()
+    names = ["czt_time", "czt_space", "stage2_gs"]
+    kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
+
+    # End to end through the host-buffer entry point, pinned host memory, copies included.
+    e2e_steps = min(args.steps, 200)
+    y_host = torch.from_numpy(y_np).pin_memory()
+    out_host = torch.empty((nblk, B, N), dtype=torch.complex64).pin_memory()
+    plan.execute_host(y_host, out_host, nblk)
+    e2e_t = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.execute_host(y_host, out_host, nblk)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    flops = flop_model(info)
+    bytes_ = alg_bytes(info)
+    per_launch_flops = {"czt_time": flops["czt_time"] * nblk, "czt_space": flops["czt_space"] * nblk,
+                        "stage2_gs": flops["stage2_gs"] * nblk}
+    dom = max(kern_ms, key=kern_ms.get)
+    achieved = per_launch_flops[dom] / (kern_ms[dom] / 1e3) / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f)
+        key = f"{w['name']}:{dom}"
+        if key in tr:
+            traffic = tr[key]
+    hbm_total_bytes = 8.0 * nblk * (M * N + B * N)
+    hbm_frac = (hbm_total_bytes / (statistics.mean(step_ms) / 1e3)) / (float(peaks["hbm_gbs"]) * 1e9)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        beams = np.linspace(0, B - 1, 32).astype(int)
+        val, t_plan, reps, _, _ = oracle_sample(w, y_np, beams, 4, budget_s=10.0)
+        cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{reps} x (4 blocks x 32 of {B} beams) of {w['name']}, FP64 numpy oracle, per-plan LU "
+                         f"of the 32 beams ({t_plan:.1f} s) excluded"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w['name']}: ULA M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
+                               f"{nblk} blocks/step per GPU, complex64",
+                   "M": M, "B": B, "N": N, "L": info.L, "nblk_per_gpu": nblk, "stage2": fb.STAGE2_NAMES[info.stage2],
+                   "l2": "flushed before every timed step (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "rel_err_vs_oracle": rel_err,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "hbm_roofline_frac": hbm_frac,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": traffic,
+                     "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
+                                    f"({peak_kind} sm_max_mhz)"},
+        "kernels_ms": kern_ms,
+        "e2e": {"value": units * e2e_steps / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},
+        "gpu_launches": plan.launch_count(nblk) * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

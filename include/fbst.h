@@ -1,0 +1,174 @@
+/*
+ * fbst.h -- C ABI of the GB300 (sm_103a) fast broadband beamspace transform (FBST).
+ *
+ * The FBST (Singh, DeLude, Davenport, Romberg, "A Fast Broadband Beamspace Transformation")
+ * forms B broadband beams from N snapshots of an M-element array. For each beam b it computes
+ * the regularised least-squares beam of Sec. III-A,
+ *
+ *     w_b    = F_b^H y                          Eq. (5)-(6); the "fan" chirp-z of Sec. IV
+ *     beta_b = (F_b^H F_b + delta I)^{-1} w_b   Eq. (5); Toeplitz, applied as in Sec. V
+ *     bhat_b = F_u beta_b                       Eq. (7); a chirp-z in n (Sec. V)
+ *
+ * Conventions shared by every entry point (all 0-based, time in samples):
+ *   - complex numbers are complex64: interleaved (re, im) float32 pairs, 8 bytes each;
+ *   - y    is [nblk][M][N]: block, element, snapshot (snapshot fastest);
+ *   - w    is [nblk][B][L]: block, beam, frequency index (frequency fastest);
+ *   - bhat is [nblk][B][N]: block, beam, output sample;
+ *   - element m of a linear array sits at m half wavelengths (at f_c + Omega) from element 0;
+ *     element s = kx*my + ky of a rectangular array sits at (kx, ky);
+ *   - beam b of a linear array looks at u_b = -1 + 2b/B (direction cosine); beam b = a*by + c of a
+ *     rectangular array looks at (u, v) = (-1 + 2a/bx, -1 + 2c/by) (Sec. IV, App. B);
+ *   - frequency index ell = 0..L-1 stands for the paper's ell = 1..L, ell' = ell + 1 - L/2, and
+ *     omega_ell*T_s = 2*pi*epsilon*ell'/L (Eq. (3)).
+ *
+ * Device pointers must be 16-byte aligned and must not overlap. Every entry point returns an
+ * fbst_status; nothing crosses the ABI as an exception. Execution entry points enqueue work on
+ * the given CUDA stream (a cudaStream_t passed as void*, NULL = legacy default stream) and return
+ * before it finishes; results are valid once the stream is synchronised. Plans are not
+ * thread-safe: calls that share a plan must not run concurrently from several host threads, and
+ * executions of one plan on different streams must not overlap in time on the GPU (they share
+ * the plan's workspace).
+ */
+#ifndef FBST_H
+#define FBST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbst_plan_s* fbst_plan_t;
+
+/* Status codes returned by every entry point. */
+enum fbst_status {
+  FBST_OK = 0,
+  FBST_ERR_INVALID = -1,     /* a size, pointer or parameter is out of range */
+  FBST_ERR_OOM = -2,         /* device or host allocation failed */
+  FBST_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+  FBST_ERR_UNSUPPORTED = -4, /* valid but not implemented (e.g. an FFT size above 4096) */
+  FBST_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  FBST_ERR_NUMERIC = -6      /* plan-time maths failed (A_b not numerically positive definite) */
+};
+
+enum fbst_array_kind { FBST_ULA = 0, FBST_URA = 1 };
+
+/* How stage 2 (beta_b = A_b^{-1} w_b followed by bhat_b = F_u beta_b) is applied. */
+enum fbst_stage2_kind {
+  FBST_STAGE2_AUTO = 0,        /* the plan picks GS_IR1 */
+  FBST_STAGE2_GS = 1,          /* Gohberg-Semencul with circulant FFTs, then chirp-z (Sec. V); in FP32
+                                  its error grows like eps32 * cond(A_b) (~2/delta_rel at broadside) */
+  FBST_STAGE2_GS_IR1 = 2,      /* GS plus one FP32 refinement step beta += GS(w - A_b beta) */
+  FBST_STAGE2_DENSE_FP32 = 3,  /* precomputed G_b = F_u A_b^{-1} (Sec. III-B), FP32 CUDA cores */
+  FBST_STAGE2_DENSE_BF16X3 = 4,/* G_b on tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
+  FBST_STAGE2_DENSE_TF32 = 5   /* G_b on tensor cores in TF32, FP32 accumulate */
+};
+
+/* Array and beam grid. M = mx*my elements, B = bx*by beams. A linear array has my = by = 1. */
+typedef struct {
+  int kind;   /* FBST_ULA or FBST_URA */
+  int mx, my; /* elements along x and y */
+  int bx, by; /* beams along u and v */
+} fbst_geometry;
+
+/* Band and basis parameters (Sec. III-A, Sec. VI). */
+typedef struct {
+  double frac_bw;     /* fractional bandwidth fb = 2*Omega/f_c, 0 < fb < 2; rounded by the plan
+                         to the nearest fraction with denominator <= 1000 (see fbst_info) */
+  double epsilon;     /* frequency stretch epsilon >= 1 of Eq. (3); rounded like frac_bw */
+  int gamma_num;      /* L = N*gamma_num/gamma_den must be an even integer (Eq. (3), gamma = L/N) */
+  int gamma_den;
+  double delta;       /* regulariser of Eq. (5): absolute, or relative (see delta_relative) */
+  int delta_relative; /* nonzero: the plan uses delta*M*N (M*N is the diagonal of F_b^H F_b) */
+  int stage2;         /* enum fbst_stage2_kind */
+  int max_blocks;     /* blocks the plan's workspace holds; larger nblk run in chunks (>= 1) */
+} fbst_band;
+
+/* Everything the plan derived from its arguments. */
+typedef struct {
+  int M, N, B, L;
+  int P_time;       /* FFT size of the temporal chirp-z (stage 1a) */
+  int S_time;       /* output splits of the temporal chirp-z (1 or 2) */
+  int P_space_x;    /* FFT size of the spatial chirp-z along x (the only axis of a linear array) */
+  int P_space_y;    /* FFT size of the spatial chirp-z along y (rectangular arrays) */
+  int P_gs;         /* circulant size of the Gohberg-Semencul products (>= 2L-1) */
+  int P_rec;        /* FFT size of the reconstruction chirp-z F_u */
+  int S_rec;        /* input splits of the reconstruction chirp-z (1 or 2) */
+  int stage2;       /* resolved enum fbst_stage2_kind */
+  double delta;     /* absolute delta used in A_b */
+  int64_t eps_num, eps_den; /* epsilon = eps_num/eps_den as used by the plan */
+  int64_t fb_num, fb_den;   /* frac_bw = fb_num/fb_den as used by the plan */
+  double rho;       /* Omega/(f_c + Omega) = fb/(2+fb): delay per element per unit direction cosine */
+  double snapshot_bound; /* right-hand side of Eq. (8) in samples */
+  double gamma_bound;    /* right-hand side of Eq. (4) */
+  int warn_snapshots;    /* 1 if N does not exceed the Eq. (8) bound */
+  int warn_gamma;        /* 1 if gamma does not exceed the Eq. (4) bound */
+  size_t table_bytes;     /* device bytes of the plan's tables */
+  size_t workspace_bytes; /* device bytes of the plan's per-call workspace */
+} fbst_info;
+
+/* Host-only: derive the plan parameters without touching a GPU. Same validation as fbst_plan.
+ * M and B must equal mx*my and bx*by. Returns FBST_ERR_INVALID / FBST_ERR_UNSUPPORTED on bad
+ * input and fills *out otherwise. */
+int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fbst_band* band, fbst_info* out);
+
+/* Build a plan on the current CUDA device: chirp tables and Bluestein kernel spectra (exact
+ * integer reduction of the quadratic phases, FP64), Toeplitz generators of every A_b (Sec. V),
+ * FP64 Levinson solves for the first column of A_b^{-1}, and either the Gohberg-Semencul spectra
+ * or the dense operators G_b = F_u A_b^{-1}. Plan-time kernels run on `stream` and the call
+ * synchronises it before returning. The plan owns all of its device memory. */
+int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band,
+              void* stream);
+
+/* Whole transform: y (device, [nblk][M][N]) -> bhat (device, [nblk][B][N]). nblk = 0 is a no-op.
+ * Blocks are independent contiguous batches of N snapshots (Sec. III-A, streaming paragraph). */
+int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
+
+/* Same as fbst_execute with HOST buffers (pinned or pageable): copies y in, runs, copies bhat out,
+ * all on `stream`, and synchronises the stream before returning. Uses plan-owned staging memory
+ * (allocated on the first call). */
+int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream);
+
+/* Stage 1 alone, the fan chirp-z of Sec. IV (App. B for rectangular arrays):
+ * y (device, [nblk][M][N]) -> w (device, [nblk][B][L]), w_b = F_b^H y. */
+int fbst_czt(fbst_plan_t p, const void* y, void* w, int nblk, void* stream);
+
+/* The temporal chirp-z of Sec. IV alone: yhat[blk][ell][m] = sum_n y[blk][m][n] e^{-j omega_ell n}
+ * (device, [nblk][L][M], element fastest). Exposed for stage-level testing. */
+int fbst_czt_time(fbst_plan_t p, const void* y, void* yhat, int nblk, void* stream);
+
+/* The spatial chirp-z of Sec. IV (App. B) alone: yhat (device, [nblk][L][M], as written by
+ * fbst_czt_time) -> w (device, [nblk][B][L]). fbst_czt_time followed by fbst_czt_space equals
+ * fbst_czt. Exposed for stage-level testing and timing. */
+int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* stream);
+
+/* Stage 2 alone (Sec. V): w (device, [nblk][B][L]) -> bhat (device, [nblk][B][N]),
+ * bhat_b = F_u (F_b^H F_b + delta I)^{-1} w_b, with the plan's stage-2 variant. */
+int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream);
+
+/* Copy the derived parameters of a plan. */
+int fbst_plan_info(fbst_plan_t p, fbst_info* out);
+
+/* Copy the first column x_b of A_b^{-1} for every beam (FP64 Levinson result, Sec. V) to host
+ * memory `x_host` as [B][L] complex128 (interleaved doubles). Exposed for testing. */
+int fbst_plan_generators(fbst_plan_t p, void* x_host);
+
+/* Free the plan and all of its device memory. Waits for the plan's outstanding work. NULL is OK. */
+int fbst_destroy(fbst_plan_t p);
+
+/* Static human-readable name of a status code. */
+const char* fbst_status_string(int status);
+
+/* Description of the last CUDA failure seen by this host thread ("" if none). The string is owned
+ * by the library and stays valid until the next failing call on the same thread. */
+const char* fbst_last_error(void);
+
+/* Number of kernels one fbst_execute of nblk blocks launches (for launch accounting). */
+int fbst_launch_count(fbst_plan_t p, int nblk);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBST_H */

@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) fast broadband beamspace transform: CUDA library + thin Python binding."""
+from ._native import (  # noqa: F401
+    FBSTError,
+    Band,
+    Geometry,
+    Info,
+    Plan,
+    STAGE2,
+    STAGE2_NAMES,
+    derive,
+    load_library,
+    make_band,
+    make_geometry,
+)

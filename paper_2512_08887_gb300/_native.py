@@ -1,0 +1,215 @@
+"""ctypes binding of libfbst.so (include/fbst.h): argument marshalling only.
+
+Every step of the transform runs in the CUDA library. This module converts Python arguments to
+the C structs, passes device pointers (torch tensors' data_ptr or plain integers) and the CUDA
+stream through, and turns status codes into exceptions. There is no CPU or PyTorch fallback: if
+the library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfbst.so")
+
+FBST_OK = 0
+STATUS_NAMES = {0: "FBST_OK", -1: "FBST_ERR_INVALID", -2: "FBST_ERR_OOM", -3: "FBST_ERR_CUDA",
+                -4: "FBST_ERR_UNSUPPORTED", -5: "FBST_ERR_TIMEOUT", -6: "FBST_ERR_NUMERIC"}
+ULA, URA = 0, 1
+STAGE2 = {"auto": 0, "gs": 1, "gs_ir1": 2, "dense_fp32": 3, "dense_bf16x3": 4, "dense_tf32": 5}
+STAGE2_NAMES = {v: k for k, v in STAGE2.items()}
+
+
+class FBSTError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = f"{what} failed: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class Geometry(C.Structure):
+    _fields_ = [("kind", C.c_int), ("mx", C.c_int), ("my", C.c_int), ("bx", C.c_int), ("by", C.c_int)]
+
+
+class Band(C.Structure):
+    _fields_ = [("frac_bw", C.c_double), ("epsilon", C.c_double), ("gamma_num", C.c_int),
+                ("gamma_den", C.c_int), ("delta", C.c_double), ("delta_relative", C.c_int),
+                ("stage2", C.c_int), ("max_blocks", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("M", C.c_int), ("N", C.c_int), ("B", C.c_int), ("L", C.c_int),
+                ("P_time", C.c_int), ("S_time", C.c_int), ("P_space_x", C.c_int), ("P_space_y", C.c_int),
+                ("P_gs", C.c_int), ("P_rec", C.c_int), ("S_rec", C.c_int), ("stage2", C.c_int),
+                ("delta", C.c_double), ("eps_num", C.c_int64), ("eps_den", C.c_int64),
+                ("fb_num", C.c_int64), ("fb_den", C.c_int64), ("rho", C.c_double),
+                ("snapshot_bound", C.c_double), ("gamma_bound", C.c_double),
+                ("warn_snapshots", C.c_int), ("warn_gamma", C.c_int),
+                ("table_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+# Every symbol include/fbst.h declares, with its ctypes signature.
+_VP, _I = C.c_void_p, C.c_int
+SIGNATURES = {
+    "fbst_derive": (_I, [C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), C.POINTER(Info)]),
+    "fbst_plan": (_I, [C.POINTER(_VP), C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), _VP]),
+    "fbst_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_execute_host": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_czt": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_czt_time": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_czt_space": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_toeplitz_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_plan_info": (_I, [_VP, C.POINTER(Info)]),
+    "fbst_plan_generators": (_I, [_VP, _VP]),
+    "fbst_destroy": (_I, [_VP]),
+    "fbst_status_string": (C.c_char_p, [_I]),
+    "fbst_last_error": (C.c_char_p, []),
+    "fbst_launch_count": (_I, [_VP, _I]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libfbst.so once (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2512_08887_gb300.build` "
+                               "(the FBST has no CPU fallback)")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != FBST_OK:
+        lib = load_library()
+        detail = lib.fbst_last_error().decode() if status == -3 else ""
+        raise FBSTError(status, what, detail)
+
+
+def _ptr(x) -> int:
+    """Device/host address of a torch tensor, a numpy array or a plain integer."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_geometry(kind: str, mx: int, my: int = 1, bx: int | None = None, by: int | None = None) -> Geometry:
+    k = ULA if kind == "ula" else URA
+    return Geometry(k, mx, my, mx if bx is None else bx, (my if k == URA else 1) if by is None else by)
+
+
+def make_band(frac_bw: float, epsilon: float = 1.01, gamma=(2, 1), delta: float = 1e-3,
+              delta_relative: bool = True, stage2: str = "auto", max_blocks: int = 64) -> Band:
+    return Band(float(frac_bw), float(epsilon), int(gamma[0]), int(gamma[1]), float(delta),
+                int(bool(delta_relative)), STAGE2[stage2], int(max_blocks))
+
+
+def derive(geom: Geometry, N: int, band: Band) -> Info:
+    """Host-only parameter derivation (fbst_derive); raises FBSTError on invalid input."""
+    lib = load_library()
+    info = Info()
+    M, B = geom.mx * geom.my, geom.bx * geom.by
+    _check(lib.fbst_derive(C.byref(geom), M, N, B, C.byref(band), C.byref(info)), "fbst_derive")
+    return info
+
+
+class Plan:
+    """An FBST plan on the current CUDA device (fbst_plan / fbst_destroy)."""
+
+    def __init__(self, geom: Geometry, N: int, band: Band, stream=None):
+        self._lib = load_library()
+        self.geom, self.band = geom, band
+        self.M, self.B, self.N = geom.mx * geom.my, geom.bx * geom.by, N
+        h = C.c_void_p()
+        _check(self._lib.fbst_plan(C.byref(h), C.byref(geom), self.M, N, self.B, C.byref(band),
+                                   _stream(stream)), "fbst_plan")
+        self._h = h
+        self.info = Info()
+        _check(self._lib.fbst_plan_info(self._h, C.byref(self.info)), "fbst_plan_info")
+        self.L = self.info.L
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def _call(self, name: str, src, dst, nblk: int, stream) -> None:
+        _check(getattr(self._lib, name)(self._h, _ptr(src), _ptr(dst), int(nblk), _stream(stream)), name)
+
+    def execute(self, y, bhat, nblk: int, stream=None) -> None:
+        """y [nblk][M][N] -> bhat [nblk][B][N], complex64 device buffers."""
+        self._call("fbst_execute", y, bhat, nblk, stream)
+
+    def execute_host(self, y, bhat, nblk: int, stream=None) -> None:
+        """Same with host buffers (copies inside, synchronises the stream)."""
+        self._call("fbst_execute_host", y, bhat, nblk, stream)
+
+    def czt(self, y, w, nblk: int, stream=None) -> None:
+        """Stage 1: y [nblk][M][N] -> w [nblk][B][L]."""
+        self._call("fbst_czt", y, w, nblk, stream)
+
+    def czt_time(self, y, yhat, nblk: int, stream=None) -> None:
+        """Temporal chirp-z only: y [nblk][M][N] -> yhat [nblk][L][M]."""
+        self._call("fbst_czt_time", y, yhat, nblk, stream)
+
+    def czt_space(self, yhat, w, nblk: int, stream=None) -> None:
+        """Spatial chirp-z only: yhat [nblk][L][M] -> w [nblk][B][L]."""
+        self._call("fbst_czt_space", yhat, w, nblk, stream)
+
+    def toeplitz_apply(self, w, bhat, nblk: int, stream=None) -> None:
+        """Stage 2: w [nblk][B][L] -> bhat [nblk][B][N]."""
+        self._call("fbst_toeplitz_apply", w, bhat, nblk, stream)
+
+    def launch_count(self, nblk: int) -> int:
+        return int(self._lib.fbst_launch_count(self._h, int(nblk)))
+
+    def generators(self):
+        """First column of every A_b^{-1} from the FP64 Levinson solve, numpy complex128 [B][L]."""
+        import numpy as np
+        out = np.empty((self.B, self.L), dtype=np.complex128)
+        _check(self._lib.fbst_plan_generators(self._h, out.ctypes.data), "fbst_plan_generators")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fbst_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,272 @@
+// C ABI of the FBST library (include/fbst.h): plan lifetime, execution and status reporting.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace fbst {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorName(e), what, file, line);
+}
+
+template <typename T>
+static int dmalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return FBST_OK;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    cudaGetLastError();  // clear the sticky-free error state of a failed allocation
+    return e == cudaErrorMemoryAllocation ? FBST_ERR_OOM : FBST_ERR_CUDA;
+  }
+  return FBST_OK;
+}
+
+static void free_plan_memory(fbst_plan_s* p) {
+  void* ptrs[] = {p->tw32, p->tw64, p->pre_t, p->gspec_t, p->post_t,
+                  p->ax[0].pre, p->ax[0].kspec, p->ax[0].post,
+                  p->same_axes ? nullptr : p->ax[1].pre, p->same_axes ? nullptr : p->ax[1].kspec,
+                  p->same_axes ? nullptr : p->ax[1].post,
+                  p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, p->G, p->Gtc, p->x64,
+                  p->ws_yhat, p->ws_w, p->ws_tc, p->stage_y, p->stage_bhat, p->d_status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+static int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s) {
+  switch (p->info.stage2) {
+    case FBST_STAGE2_GS:
+    case FBST_STAGE2_GS_IR1: return launch_stage2_gs(p, w, bhat, nb, s);
+    case FBST_STAGE2_DENSE_FP32: return launch_stage2_dense_fp32(p, w, bhat, nb, s);
+    case FBST_STAGE2_DENSE_BF16X3:
+    case FBST_STAGE2_DENSE_TF32: return launch_stage2_dense_tc(p, w, bhat, nb, s);
+    default: return FBST_ERR_INVALID;
+  }
+}
+
+static int check_exec_args(fbst_plan_s* p, const void* in, void* out, int nblk) {
+  if (!p || nblk < 0) return FBST_ERR_INVALID;
+  if (nblk == 0) return FBST_OK;
+  if (!in || !out || !aligned16(in) || !aligned16(out)) return FBST_ERR_INVALID;
+  return FBST_OK;
+}
+
+#define FBST_TRY(expr)          \
+  do {                          \
+    const int fbst_r_ = (expr); \
+    if (fbst_r_ != FBST_OK) return fbst_r_; \
+  } while (0)
+
+}  // namespace fbst
+
+using namespace fbst;
+
+extern "C" {
+
+const char* fbst_status_string(int status) {
+  switch (status) {
+    case FBST_OK: return "FBST_OK";
+    case FBST_ERR_INVALID: return "FBST_ERR_INVALID: a size, pointer or parameter is out of range";
+    case FBST_ERR_OOM: return "FBST_ERR_OOM: allocation failed";
+    case FBST_ERR_CUDA: return "FBST_ERR_CUDA: a CUDA call failed";
+    case FBST_ERR_UNSUPPORTED: return "FBST_ERR_UNSUPPORTED: valid but not supported by this build";
+    case FBST_ERR_TIMEOUT: return "FBST_ERR_TIMEOUT: a bounded device wait gave up";
+    case FBST_ERR_NUMERIC: return "FBST_ERR_NUMERIC: a Toeplitz system is not numerically positive definite";
+    default: return "unknown fbst status";
+  }
+}
+
+const char* fbst_last_error(void) { return g_last_error; }
+
+int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band, void* stream) {
+  if (!out) return FBST_ERR_INVALID;
+  *out = nullptr;
+  fbst_info info;
+  FBST_TRY(fbst_derive(g, M, N, B, band, &info));
+  if (g->kind == FBST_URA && info.P_space_x != info.P_space_y) return FBST_ERR_UNSUPPORTED;
+  fbst_plan_s* p = new (std::nothrow) fbst_plan_s();
+  if (!p) return FBST_ERR_OOM;
+  std::memset(p, 0, sizeof(*p));
+  p->info = info;
+  p->geom = *g;
+  p->band = *band;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int r = FBST_OK;
+  do {
+    if (cudaGetDevice(&p->device) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    const int L = info.L;
+    if ((r = dmalloc(&p->tw32, kTwiddleSize)) != FBST_OK) break;
+    if ((r = dmalloc(&p->tw64, kTwiddleSize)) != FBST_OK) break;
+    if ((r = dmalloc(&p->pre_t, info.N)) != FBST_OK) break;
+    if ((r = dmalloc(&p->gspec_t, (size_t)info.S_time * info.P_time)) != FBST_OK) break;
+    if ((r = dmalloc(&p->post_t, L)) != FBST_OK) break;
+    p->ax[0] = fbst_axis_tables{g->mx, g->bx, info.P_space_x, nullptr, nullptr, nullptr};
+    p->n_axes = 1;
+    p->same_axes = 1;
+    if (g->kind == FBST_URA) {
+      p->ax[1] = fbst_axis_tables{g->my, g->by, info.P_space_y, nullptr, nullptr, nullptr};
+      if (!(g->mx == g->my && g->bx == g->by)) {
+        p->n_axes = 2;
+        p->same_axes = 0;
+      }
+    }
+    for (int a = 0; a < p->n_axes && r == FBST_OK; ++a) {
+      fbst_axis_tables& ax = p->ax[a];
+      if ((r = dmalloc(&ax.pre, (size_t)L * ax.Ma)) != FBST_OK) break;
+      if ((r = dmalloc(&ax.kspec, (size_t)L * ax.P)) != FBST_OK) break;
+      if ((r = dmalloc(&ax.post, (size_t)L * ax.Ba)) != FBST_OK) break;
+    }
+    if (r != FBST_OK) break;
+    if (p->same_axes && g->kind == FBST_URA) {
+      p->ax[1].pre = p->ax[0].pre;
+      p->ax[1].kspec = p->ax[0].kspec;
+      p->ax[1].post = p->ax[0].post;
+    }
+    if ((r = dmalloc(&p->x64, (size_t)B * L)) != FBST_OK) break;
+    if (info.stage2 == FBST_STAGE2_GS || info.stage2 == FBST_STAGE2_GS_IR1) {
+      if ((r = dmalloc(&p->XV, (size_t)B * 2 * info.P_gs)) != FBST_OK) break;
+      if (info.stage2 == FBST_STAGE2_GS_IR1 && (r = dmalloc(&p->Aspec, (size_t)B * info.P_gs)) != FBST_OK) break;
+      if ((r = dmalloc(&p->pre_r, (size_t)L)) != FBST_OK) break;
+      if ((r = dmalloc(&p->qspec_r, (size_t)info.S_rec * info.P_rec)) != FBST_OK) break;
+      if ((r = dmalloc(&p->post_r, (size_t)info.N)) != FBST_OK) break;
+    } else {
+      if ((r = dmalloc(&p->G, (size_t)B * info.N * L)) != FBST_OK) break;
+    }
+    if ((r = dmalloc(&p->ws_yhat, (size_t)band->max_blocks * L * M)) != FBST_OK) break;
+    if ((r = dmalloc(&p->ws_w, (size_t)band->max_blocks * B * L)) != FBST_OK) break;
+    if ((r = dmalloc(&p->d_status, 1)) != FBST_OK) break;
+    if (cudaMemsetAsync(p->d_status, 0, sizeof(int), s) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    r = build_plan_tables(p, s);
+  } while (0);
+  if (r != FBST_OK) {
+    cudaStreamSynchronize(s);
+    free_plan_memory(p);
+    delete p;
+    return r;
+  }
+  *out = p;
+  return FBST_OK;
+}
+
+int fbst_destroy(fbst_plan_t p) {
+  if (!p) return FBST_OK;
+  cudaDeviceSynchronize();
+  free_plan_memory(p);
+  delete p;
+  return FBST_OK;
+}
+
+int fbst_plan_info(fbst_plan_t p, fbst_info* out) {
+  if (!p || !out) return FBST_ERR_INVALID;
+  *out = p->info;
+  return FBST_OK;
+}
+
+int fbst_plan_generators(fbst_plan_t p, void* x_host) {
+  if (!p || !x_host) return FBST_ERR_INVALID;
+  FBST_CUDA_TRY(cudaMemcpy(x_host, p->x64, sizeof(double2) * (size_t)p->info.B * p->info.L, cudaMemcpyDeviceToHost));
+  return FBST_OK;
+}
+
+int fbst_czt_time(fbst_plan_t p, const void* y, void* yhat, int nblk, void* stream) {
+  FBST_TRY(check_exec_args(p, y, yhat, nblk));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  for (int c0 = 0; c0 < nblk; c0 += 65535) {
+    const int nb = std::min(65535, nblk - c0);
+    FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N,
+                             static_cast<float2*>(yhat) + (size_t)c0 * in.L * in.M, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* stream) {
+  FBST_TRY(check_exec_args(p, yhat, w, nblk));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  for (int c0 = 0; c0 < nblk; c0 += 65535) {
+    const int nb = std::min(65535, nblk - c0);
+    FBST_TRY(launch_czt_space(p, static_cast<const float2*>(yhat) + (size_t)c0 * in.L * in.M,
+                              static_cast<float2*>(w) + (size_t)c0 * in.B * in.L, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_czt(fbst_plan_t p, const void* y, void* w, int nblk, void* stream) {
+  FBST_TRY(check_exec_args(p, y, w, nblk));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  const int maxb = p->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
+    FBST_TRY(launch_czt_space(p, p->ws_yhat, static_cast<float2*>(w) + (size_t)c0 * in.B * in.L, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream) {
+  FBST_TRY(check_exec_args(p, w, bhat, nblk));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  const int maxb = p->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    FBST_TRY(run_stage2(p, static_cast<const float2*>(w) + (size_t)c0 * in.B * in.L,
+                        static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream) {
+  FBST_TRY(check_exec_args(p, y, bhat, nblk));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  const int maxb = p->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
+    FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nb, s));
+    FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream) {
+  if (!p || nblk < 0) return FBST_ERR_INVALID;
+  if (nblk == 0) return FBST_OK;
+  if (!y_host || !bhat_host) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = p->info;
+  const int maxb = p->band.max_blocks;
+  if (!p->stage_y) FBST_TRY(dmalloc(&p->stage_y, (size_t)maxb * in.M * in.N));
+  if (!p->stage_bhat) FBST_TRY(dmalloc(&p->stage_bhat, (size_t)maxb * in.B * in.N));
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    const size_t ybytes = sizeof(float2) * (size_t)nb * in.M * in.N;
+    const size_t bbytes = sizeof(float2) * (size_t)nb * in.B * in.N;
+    FBST_CUDA_TRY(cudaMemcpyAsync(p->stage_y, static_cast<const char*>(y_host) + sizeof(float2) * (size_t)c0 * in.M * in.N,
+                                  ybytes, cudaMemcpyHostToDevice, s));
+    FBST_TRY(fbst_execute(p, p->stage_y, p->stage_bhat, nb, stream));
+    FBST_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(bhat_host) + sizeof(float2) * (size_t)c0 * in.B * in.N, p->stage_bhat,
+                                  bbytes, cudaMemcpyDeviceToHost, s));
+  }
+  FBST_CUDA_TRY(cudaStreamSynchronize(s));
+  return FBST_OK;
+}
+
+int fbst_launch_count(fbst_plan_t p, int nblk) {
+  if (!p || nblk <= 0) return 0;
+  const int chunks = (nblk + p->band.max_blocks - 1) / p->band.max_blocks;
+  return chunks * (2 + stage2_launches(p));
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Shared definitions of the FBST CUDA library: complex helpers, the plan object and error macros.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fbst.h"
+
+namespace fbst {
+
+// ---------------------------------------------------------------------------------------------
+// Complex arithmetic on float2 / double2 (x = real, y = imaginary).
+// ---------------------------------------------------------------------------------------------
+template <typename R> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename V> __host__ __device__ __forceinline__ V cmulc(V a, V b) {
+  return V{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
+template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) {
+  return V{a.x * s, a.y * s};
+}
+
+// Largest FFT size of any table or kernel, and the size of the shared twiddle tables
+// (tw[m] = exp(-2*pi*i*m/kTwiddleSize), built in FP64 at plan time).
+constexpr int kMaxFFT = 4096;
+constexpr int kTwiddleSize = 4096;
+
+}  // namespace fbst
+
+// ---------------------------------------------------------------------------------------------
+// The plan. All pointers are device memory owned by the plan unless stated otherwise.
+// ---------------------------------------------------------------------------------------------
+struct fbst_axis_tables {
+  int Ma, Ba, P;       // elements along the axis, beams along the axis, Bluestein FFT size
+  float2* pre;         // [L][Ma]   chirp premultiply (includes the -kappa*m steering offset)
+  float2* kspec;       // [L][P]    FFT of the Bluestein kernel, scaled by 1/P
+  float2* post;        // [L][Ba]   chirp postmultiply
+};
+
+struct fbst_plan_s {
+  fbst_info info;
+  fbst_geometry geom;
+  fbst_band band;
+  int device;
+
+  float2* tw32;        // [kTwiddleSize] exp(-2*pi*i*m/kTwiddleSize) rounded to float
+  double2* tw64;       // same in double (plan-time FFTs)
+
+  // Stage 1a: temporal chirp-z (N snapshots -> L frequencies), S_time output splits.
+  float2* pre_t;       // [N]
+  float2* gspec_t;     // [S_time][P_time], scaled by 1/P_time
+  float2* post_t;      // [L]
+
+  // Stage 1b: spatial chirp-z per frequency; axis 0 = x (all arrays), axis 1 = y (rectangular).
+  fbst_axis_tables ax[2];
+  int n_axes;
+  int same_axes;       // 1 if the y axis reuses axis 0's tables
+
+  // Stage 2, Gohberg-Semencul: spectra of x_b and of Z J conj(x_b), both / (sqrt(x_0) * P_gs),
+  // stored together per beam: XV[b][0][k] = X_b[k], XV[b][1][k] = V_b[k].
+  float2* XV;          // [B][2][P_gs]
+  // Spectrum of the circulant embedding of A_b (size P_gs), / P_gs, for the refinement step.
+  float2* Aspec;       // [B][P_gs] (GS_IR1 only)
+  // Reconstruction chirp-z F_u (L coefficients -> N samples), S_rec input splits.
+  float2* pre_r;       // [S_rec][L/S_rec]
+  float2* qspec_r;     // [S_rec][P_rec], scaled by 1/P_rec
+  float2* post_r;      // [N]
+
+  // Stage 2, dense: G_b = F_u A_b^{-1}.
+  float2* G;           // [B][N][L] complex64 (DENSE_FP32)
+  void* Gtc;           // tensor-core operand (split-BF16 or TF32 layout), see dense_tc.cu
+  size_t Gtc_bytes;
+
+  double2* x64;        // [B][L] first column of A_b^{-1} (FP64), kept for inspection
+
+  // Per-call workspace, max_blocks blocks.
+  float2* ws_yhat;     // [max_blocks][L][M]
+  float2* ws_w;        // [max_blocks][B][L]
+  void* ws_tc;         // tensor-core right-hand-side operand (dense TC variants)
+  size_t ws_tc_bytes;
+
+  // Host-buffer staging (fbst_execute_host), allocated on first use.
+  float2* stage_y;     // [max_blocks][M][N]
+  float2* stage_bhat;  // [max_blocks][B][N]
+
+  int* d_status;       // device status word (FP64 plan kernels report here)
+};
+
+#define FBST_CUDA_TRY(expr)                                  \
+  do {                                                       \
+    cudaError_t fbst_e_ = (expr);                            \
+    if (fbst_e_ != cudaSuccess) {                            \
+      fbst::set_last_cuda_error(fbst_e_, #expr, __FILE__, __LINE__); \
+      return FBST_ERR_CUDA;                                  \
+    }                                                        \
+  } while (0)
+
+namespace fbst {
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Kernel launchers (each returns an fbst_status). All run on `s`.
+int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk, cudaStream_t s);
+int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s);
+int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+int stage2_launches(const fbst_plan_s* p);
+
+// Plan-time builders (plan.cu / dense_tc.cu).
+int build_plan_tables(fbst_plan_s* p, cudaStream_t s);
+int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s);
+}  // namespace fbst

@@ -1,0 +1,154 @@
+// Block-cooperative complex FFTs held in registers, exchanged through shared memory.
+//
+// A transform of size P (a power of two, 2..4096) is owned by T = P/E threads of one CTA; thread
+// t (0 <= t < T) holds the E elements with indices t + T*r, r = 0..E-1, in v[r]. That layout is
+// both the input and the output layout, so pointwise work (chirps, spectra) happens in registers.
+// The transform is a Stockham autosort decimation-in-time FFT: every pass reads radix-R groups
+// at stride P/R straight from registers, applies the twiddles exp(dir*2*pi*i*s*k/(Ns*R)) from an
+// FP64-built table, does a radix-R DFT in registers, and scatters its R outputs to shared memory in
+// Stockham order; after a barrier each thread reloads its E elements at stride T. R = E except for
+// a final smaller pass when P is not a power of E. Shared memory is padded by one element per 128
+// bytes so that the stride-R scatter of the early passes does not serialise on banks.
+//
+// All threads of the CTA must call the same transform the same number of times (the passes use
+// __syncthreads()); several groups of T threads may run independent transforms of the same size
+// in lockstep, each on its own shared buffer. Inverse transforms are not normalised: every
+// 1/P factor is folded into the plan's tables.
+#pragma once
+
+#include "common.cuh"
+
+namespace fbst {
+
+template <typename V> struct fft_pad {
+  // One padding element per 128 bytes.
+  static constexpr int shift = (sizeof(V) == 8) ? 4 : 3;
+  __device__ __forceinline__ static int at(int i) { return i + (i >> shift); }
+  static constexpr int words(int P) { return P + (P >> shift) + 1; }
+};
+
+// Shared-memory elements one transform of size P needs.
+template <typename V> constexpr int fft_smem_elems(int P) { return fft_pad<V>::words(P); }
+
+// cos(2*pi*j/16), j = 0..15, for the in-register butterflies.
+__host__ __device__ constexpr double cos16(int j) {
+  constexpr double c1 = 0.92387953251128675613, c2 = 0.70710678118654752440,
+                   c3 = 0.38268343236508977173;
+  switch (((j % 16) + 16) % 16) {
+    case 0: return 1.0;   case 1: return c1;   case 2: return c2;   case 3: return c3;
+    case 4: return 0.0;   case 5: return -c3;  case 6: return -c2;  case 7: return -c1;
+    case 8: return -1.0;  case 9: return -c1;  case 10: return -c2; case 11: return -c3;
+    case 12: return 0.0;  case 13: return c3;  case 14: return c2;  default: return c1;
+  }
+}
+
+// a * exp(DIR*2*pi*i*K/R) for a compile-time root (R divides 16).
+template <int R, int K, int DIR, typename V>
+__device__ __forceinline__ V mul_root(V a) {
+  constexpr int k = ((K % R) + R) % R;
+  using S = decltype(a.x);
+  if constexpr (k == 0) {
+    return a;
+  } else if constexpr (2 * k == R) {
+    return V{-a.x, -a.y};
+  } else if constexpr (4 * k == R) {
+    return DIR < 0 ? V{a.y, -a.x} : V{-a.y, a.x};
+  } else if constexpr (4 * k == 3 * R) {
+    return DIR < 0 ? V{-a.y, a.x} : V{a.y, -a.x};
+  } else {
+    constexpr int j = k * (16 / R);
+    constexpr S c = static_cast<S>(cos16(j));
+    constexpr S s = static_cast<S>(DIR * cos16(j - 4));  // sin(2*pi*j/16) = cos(2*pi*(j-4)/16)
+    return V{a.x * c - a.y * s, a.x * s + a.y * c};
+  }
+}
+
+template <int R, int DIR, int K, typename V>
+__device__ __forceinline__ void dft_combine(V* x, const V* e, const V* o) {
+  if constexpr (K < R / 2) {
+    const V t = mul_root<R, K, DIR>(o[K]);
+    x[K] = cadd(e[K], t);
+    x[K + R / 2] = csub(e[K], t);
+    dft_combine<R, DIR, K + 1>(x, e, o);
+  }
+}
+
+// In-register DFT of size R (1, 2, 4, 8 or 16): x[k] <- sum_n x[n] exp(DIR*2*pi*i*n*k/R).
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void dft(V* x) {
+  if constexpr (R == 2) {
+    const V a = x[0];
+    x[0] = cadd(a, x[1]);
+    x[1] = csub(a, x[1]);
+  } else if constexpr (R > 2) {
+    V e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    dft<R / 2, DIR>(e);
+    dft<R / 2, DIR>(o);
+    dft_combine<R, DIR, 0>(x, e, o);
+  }
+}
+
+// One Stockham pass (current sub-transform size NS) followed by the remaining passes.
+// v[f][r] is element t + T*r of transform f; sbuf holds NF consecutive padded buffers.
+template <int P, int E, int NF, int DIR, int NS, typename V>
+__device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t) {
+  if constexpr (NS < P) {
+    constexpr int R = (P / NS < E) ? (P / NS) : E;
+    constexpr int T = P / E;
+    constexpr int Q = E / R;                       // butterflies per thread in this pass
+    constexpr int TW_STRIDE = kTwiddleSize / (NS * R);
+    constexpr int SB = fft_pad<V>::words(P);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = t + T * q;                     // butterfly index, 0 <= j < P/R
+      const int k = j & (NS - 1);                  // position inside the current sub-transform
+      V w[R];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int s = 1; s < R; ++s) {
+          V ws = tw[s * k * TW_STRIDE];
+          if constexpr (DIR > 0) ws.y = -ws.y;
+          w[s] = ws;
+        }
+      }
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        V x[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) x[s] = v[f][q + Q * s];
+        if constexpr (NS > 1) {
+#pragma unroll
+          for (int s = 1; s < R; ++s) x[s] = cmul(x[s], w[s]);
+        }
+        dft<R, DIR>(x);
+#pragma unroll
+        for (int s = 0; s < R; ++s) sbuf[f * SB + fft_pad<V>::at(base + s * NS)] = x[s];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+      for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + fft_pad<V>::at(t + T * r)];
+    }
+    __syncthreads();
+    fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t);
+  }
+}
+
+// NF simultaneous transforms of size P in the strided register layout described above.
+// DIR = -1: forward (exp(-i...)); DIR = +1: unnormalised inverse. sbuf: NF*fft_smem_elems(P).
+template <int P, int E, int NF, int DIR, typename V>
+__device__ __forceinline__ void block_fft(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t) {
+  static_assert((P & (P - 1)) == 0 && P >= 2 && P <= kMaxFFT, "P must be a power of two <= 4096");
+  static_assert(E >= 2 && E <= 16 && (E & (E - 1)) == 0 && E <= P, "E must be a power of two <= 16");
+  fft_passes<P, E, NF, DIR, 1>(v, sbuf, tw, t);
+}
+
+}  // namespace fbst

@@ -1,0 +1,238 @@
+// Stage 2 of the FBST (Sec. V): beta_b = A_b^{-1} w_b, bhat_b = F_u beta_b.
+//
+// k_stage2_gs fuses, per (beam, block): the Gohberg-Semencul product (gs.cuh, six transforms of
+// size P_gs >= 2L-1) and the reconstruction chirp-z of F_u (Eq. (7)) evaluated by Bluestein
+// with S_rec input splits (S_rec forward transforms of size P_rec summed in frequency, one inverse).
+// One CTA owns one beam and a run of blocks; the beam's spectra stay in registers across blocks,
+// beta never leaves shared memory, and the only HBM traffic is w in and bhat out.
+//
+// k_dense_fp32 applies the precomputed G_b = F_u A_b^{-1} (N x L, Sec. III-B) as a batched
+// complex GEMM over blocks on the FP32 CUDA cores.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "gs.cuh"
+
+namespace fbst {
+
+template <int P> struct gs_e { static constexpr int value = P >= 4096 ? 16 : (P >= 16 ? 8 : 2); };
+
+template <int PG, int PR, int SR, bool IR>
+__global__ void __launch_bounds__(PG / gs_e<PG>::value)
+k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float2* __restrict__ XV,
+            const float2* __restrict__ Aspec,
+            const float2* __restrict__ pre_r, const float2* __restrict__ qspec, const float2* __restrict__ post_r,
+            const float2* __restrict__ tw, int B, int L, int N, int nblk, int blk_per_cta) {
+  constexpr int EG = gs_e<PG>::value;
+  constexpr int T = PG / EG;
+  constexpr int ER = PR / T;
+  static_assert(ER >= 2 && ER * T == PR, "reconstruction transform must span the same threads");
+  constexpr int SBG = fft_smem_elems<float2>(PG);
+  extern __shared__ float2 sm[];
+  float2* beta_s = sm + 2 * SBG;  // [L]
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int blk0 = blockIdx.y * blk_per_cta;
+  const int blk1 = min(nblk, blk0 + blk_per_cta);
+  const int Lr = L / SR;
+
+  float2 X[EG], Vv[EG];
+  const float2* xv = XV + (size_t)b * 2 * PG;
+#pragma unroll
+  for (int r = 0; r < EG; ++r) {
+    X[r] = xv[t + T * r];
+    Vv[r] = xv[PG + t + T * r];
+  }
+
+  for (int blk = blk0; blk < blk1; ++blk) {
+    const float2* wb = w + ((size_t)blk * B + b) * L;
+    float2 v[EG];
+#pragma unroll
+    for (int r = 0; r < EG; ++r) {
+      const int i = t + T * r;
+      v[r] = i < L ? wb[i] : make_float2(0.f, 0.f);
+    }
+    gs_apply<PG, EG>(v, X, Vv, sm, tw, t, L);
+    if constexpr (IR) {
+      // One refinement step: r = w - A beta (Toeplitz product through its circulant embedding),
+      // beta += GS(r). The residual's rounding error lies mostly where A_b is small, which F_u
+      // (whose rows are rows of F_b) does not see; the GS cancellation error is removed.
+      const float2* As = Aspec + (size_t)b * PG;
+      float2 a[1][EG];
+#pragma unroll
+      for (int r = 0; r < EG; ++r) a[0][r] = (t + T * r < L) ? v[r] : make_float2(0.f, 0.f);
+      block_fft<PG, EG, 1, -1>(a, sm, tw, t);
+#pragma unroll
+      for (int r = 0; r < EG; ++r) a[0][r] = cmul(a[0][r], As[t + T * r]);
+      block_fft<PG, EG, 1, +1>(a, sm, tw, t);
+      float2 res[EG];
+#pragma unroll
+      for (int r = 0; r < EG; ++r) {
+        const int i = t + T * r;
+        res[r] = i < L ? csub(wb[i], a[0][r]) : make_float2(0.f, 0.f);
+      }
+      gs_apply<PG, EG>(res, X, Vv, sm, tw, t, L);
+#pragma unroll
+      for (int r = 0; r < EG; ++r) v[r] = cadd(v[r], res[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < EG; ++r) {
+      const int i = t + T * r;
+      if (i < L) beta_s[i] = v[r];
+    }
+    __syncthreads();
+    // Reconstruction: bhat[n] = post[n] * IFFT( sum_h FFT(beta_h * pre_h) * Q_h )[n].
+    float2 x[SR][ER];
+#pragma unroll
+    for (int h = 0; h < SR; ++h) {
+#pragma unroll
+      for (int r = 0; r < ER; ++r) {
+        const int i = t + T * r;
+        x[h][r] = i < Lr ? cmul(beta_s[h * Lr + i], pre_r[h * Lr + i]) : make_float2(0.f, 0.f);
+      }
+    }
+    block_fft<PR, ER, SR, -1>(x, sm, tw, t);
+    float2 R[1][ER];
+#pragma unroll
+    for (int r = 0; r < ER; ++r) {
+      float2 acc = cmul(x[0][r], qspec[t + T * r]);
+#pragma unroll
+      for (int h = 1; h < SR; ++h) acc = cadd(acc, cmul(x[h][r], qspec[h * PR + t + T * r]));
+      R[0][r] = acc;
+    }
+    block_fft<PR, ER, 1, +1>(R, sm, tw, t);
+    float2* ob = bhat + ((size_t)blk * B + b) * N;
+#pragma unroll
+    for (int r = 0; r < ER; ++r) {
+      const int n = t + T * r;
+      if (n < N) ob[n] = cmul(R[0][r], post_r[n]);
+    }
+  }
+}
+
+static int blocks_per_cta(int nblk, int ctas_per_block_set, int target) {
+  int chunks = std::max(1, std::min(nblk, (target + ctas_per_block_set - 1) / std::max(1, ctas_per_block_set)));
+  return (nblk + chunks - 1) / chunks;
+}
+
+template <int PG, int PR, int SR, bool IR>
+static int stage2_gs_P(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  constexpr int EG = gs_e<PG>::value;
+  constexpr int T = PG / EG;
+  const fbst_info& in = p->info;
+  const size_t smem = sizeof(float2) * (2 * (size_t)fft_smem_elems<float2>(PG) + in.L);
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_stage2_gs<PG, PR, SR, IR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int bpc = blocks_per_cta(nblk, in.B, 8 * 152);
+  const dim3 grid(in.B, (nblk + bpc - 1) / bpc);
+  k_stage2_gs<PG, PR, SR, IR><<<grid, T, smem, s>>>(w, bhat, p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, p->tw32,
+                                                in.B, in.L, in.N, nblk, bpc);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+template <int PG, bool IR>
+static int stage2_gs_PGI(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  const int PR = p->info.P_rec, SR = p->info.S_rec;
+  if constexpr (gs_e<PG>::value >= 4) {
+    if (2 * PR == PG && SR == 2) return stage2_gs_P<PG, PG / 2, 2, IR>(p, w, bhat, nblk, s);
+    if (2 * PR == PG && SR == 1) return stage2_gs_P<PG, PG / 2, 1, IR>(p, w, bhat, nblk, s);
+  }
+  if (PR == PG && SR == 1) return stage2_gs_P<PG, PG, 1, IR>(p, w, bhat, nblk, s);
+  if (PR == PG && SR == 2) return stage2_gs_P<PG, PG, 2, IR>(p, w, bhat, nblk, s);
+  return FBST_ERR_UNSUPPORTED;
+}
+
+template <int PG>
+static int stage2_gs_PG(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  return p->info.stage2 == FBST_STAGE2_GS_IR1 ? stage2_gs_PGI<PG, true>(p, w, bhat, nblk, s)
+                                              : stage2_gs_PGI<PG, false>(p, w, bhat, nblk, s);
+}
+
+int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  if (nblk <= 0) return FBST_OK;
+  if (nblk > 65535) return FBST_ERR_UNSUPPORTED;
+  switch (p->info.P_gs) {
+    case 16: return stage2_gs_PG<16>(p, w, bhat, nblk, s);
+    case 32: return stage2_gs_PG<32>(p, w, bhat, nblk, s);
+    case 64: return stage2_gs_PG<64>(p, w, bhat, nblk, s);
+    case 128: return stage2_gs_PG<128>(p, w, bhat, nblk, s);
+    case 256: return stage2_gs_PG<256>(p, w, bhat, nblk, s);
+    case 512: return stage2_gs_PG<512>(p, w, bhat, nblk, s);
+    case 1024: return stage2_gs_PG<1024>(p, w, bhat, nblk, s);
+    case 2048: return stage2_gs_PG<2048>(p, w, bhat, nblk, s);
+    case 4096: return stage2_gs_PG<4096>(p, w, bhat, nblk, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dense FP32 apply: bhat[blk][b][n] = sum_ell G[b][n][ell] * w[blk][b][ell].
+// CTA tile: 64 samples x 16 blocks of one beam, K-chunks of 32; each thread owns 4 x 1 outputs.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_dense_fp32(const float2* __restrict__ G, const float2* __restrict__ w, float2* __restrict__ bhat,
+             int B, int N, int L, int nblk) {
+  __shared__ float2 Gs[64][33];
+  __shared__ float2 Ws[16][33];
+  const int b = blockIdx.y, n0 = blockIdx.x * 64, blk0 = blockIdx.z * 16;
+  const int tid = threadIdx.x, tn = tid & 15, tb = tid >> 4;
+  float2 acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+  const float2* Gb = G + (size_t)b * N * L;
+  for (int k0 = 0; k0 < L; k0 += 32) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = tid + 256 * j, row = idx >> 5, col = idx & 31;
+      const int n = n0 + row, k = k0 + col;
+      Gs[row][col] = (n < N && k < L) ? Gb[(size_t)n * L + k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int idx = tid + 256 * j, row = idx >> 5, col = idx & 31;
+      const int blk = blk0 + row, k = k0 + col;
+      Ws[row][col] = (blk < nblk && k < L) ? w[((size_t)blk * B + b) * L + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float2 wv = Ws[tb][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 gv = Gs[tn + 16 * i][kk];
+        acc[i].x = fmaf(gv.x, wv.x, fmaf(-gv.y, wv.y, acc[i].x));
+        acc[i].y = fmaf(gv.x, wv.y, fmaf(gv.y, wv.x, acc[i].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int blk = blk0 + tb;
+  if (blk < nblk) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int n = n0 + tn + 16 * i;
+      if (n < N) bhat[((size_t)blk * B + b) * N + n] = acc[i];
+    }
+  }
+}
+
+int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  if (nblk <= 0) return FBST_OK;
+  const fbst_info& in = p->info;
+  const dim3 grid((in.N + 63) / 64, in.B, (nblk + 15) / 16);
+  if (grid.z > 65535 || grid.y > 65535) return FBST_ERR_UNSUPPORTED;
+  k_dense_fp32<<<grid, 256, 0, s>>>(p->G, w, bhat, in.B, in.N, in.L, nblk);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+int stage2_launches(const fbst_plan_s* p) {
+  switch (p->info.stage2) {
+    case FBST_STAGE2_GS:
+    case FBST_STAGE2_GS_IR1: return 1;
+    case FBST_STAGE2_DENSE_FP32: return 1;
+    default: return 2;  // tensor-core variants: operand preparation + GEMM
+  }
+}
+
+}  // namespace fbst

@@ -1,0 +1,37 @@
+"""The four synthetic workloads (array, sizes, signal recipe, seed). Data only, no transform maths.
+
+C1  linear array M=16, N=64, B=16, fb=0.5; K=3 plane waves, 20 dB; one block; seed 1001.
+C2  linear array M=256, N=256, B=256, fb=0.5; K=8 plane waves, 10 dB; one continuous record cut
+    into 64 blocks of 256 snapshots; seed 1002.
+C3  32x32 rectangular array (M=1024), N=512, 32x32 beam grid (B=1024), fb=0.3; K=16 plane waves
+    from the unit disk, 10 dB; nblk blocks of one record; seed 1003.
+C4  64 independent linear arrays, M = 2^U{5..10}, N from {128,256,512,1024}, B=M, fb ~ U[0.2,0.6]
+    rounded to 1e-3, K=4 plane waves, 15 dB, one block each, per-instance child seeds of 1004.
+Every waveform is a sum of Q sinusoids with CN(0, 1/Q) weights and uniform in-band frequencies.
+"""
+from __future__ import annotations
+
+from .planewave import ula_config, ura_config, uneven_ula_instances
+
+CONFIGS = {
+    "C1": dict(kind="ula", mx=16, my=1, bx=16, by=1, N=64, frac_bw=0.5, K=3, snr_db=20.0, seed=1001, nblk=1),
+    "C2": dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, K=8, snr_db=10.0, seed=1002, nblk=64),
+    "C3": dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, K=16, snr_db=10.0, seed=1003, nblk=16),
+}
+
+
+def config_data(name: str, nblk: int | None = None, Q: int = 256) -> dict:
+    """Generate the seeded data of C1..C3 (nblk overrides the block count)."""
+    c = dict(CONFIGS[name])
+    if nblk is not None:
+        c["nblk"] = nblk
+    if c["kind"] == "ula":
+        d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
+    else:
+        d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
+    d.update(c)
+    return d
+
+
+def c4_instances(count: int = 64, with_data: bool = True) -> list[dict]:
+    return uneven_ula_instances(1004, count=count, with_data=with_data)
