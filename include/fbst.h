@@ -130,6 +130,17 @@ int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* strea
  * (allocated on the first call). */
 int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream);
 
+/* Same result as fbst_execute for callers that cannot allocate device memory at run time (a
+ * real-time loop that must not block in the allocator, a fixed start-up memory budget, code
+ * running under stream capture). The paper has no counterpart; this is a library convenience.
+ * The intermediates live in one 64 MiB static device array of the library instead of the plan's
+ * workspace, and the call allocates nothing. Rejects (FBST_ERR_INVALID, nothing launched) a call
+ * whose intermediates, 8*nblk*(L*M + B*L) bytes, exceed 64 MiB. Its first call on a device looks
+ * up the array's address (cudaGetSymbolAddress) and should come before any stream capture. All
+ * calls share the array, so calls that overlap on the GPU race and must be serialised. Not
+ * available for the tensor-core stage-2 variants (FBST_ERR_UNSUPPORTED). */
+int fbst_execute_noalloc(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
+
 /* Stage 1 alone, the fan chirp-z of Sec. IV (App. B for rectangular arrays):
  * y (device, [nblk][M][N]) -> w (device, [nblk][B][L]), w_b = F_b^H y. */
 int fbst_czt(fbst_plan_t p, const void* y, void* w, int nblk, void* stream);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "fbst_plan": (_I, [C.POINTER(_VP), C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), _VP]),
     "fbst_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_execute_host": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_execute_noalloc": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_czt": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_czt_time": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_czt_space": (_I, [_VP, _VP, _VP, _I, _VP]),
@@ -170,6 +171,10 @@ class Plan:
     def execute_host(self, y, bhat, nblk: int, stream=None) -> None:
         """Same with host buffers (copies inside, synchronises the stream)."""
         self._call("fbst_execute_host", y, bhat, nblk, stream)
+
+    def execute_noalloc(self, y, bhat, nblk: int, stream=None) -> None:
+        """Same as execute, intermediates in the library's static device array (no allocation)."""
+        self._call("fbst_execute_noalloc", y, bhat, nblk, stream)
 
     def czt(self, y, w, nblk: int, stream=None) -> None:
         """Stage 1: y [nblk][M][N] -> w [nblk][B][L]."""
