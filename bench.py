@@ -328,11 +328,14 @@ def main() -> None:
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
+        import hashlib
         with open(tfile) as f:
             tr = json.load(f)
-        key = f"{w['name']}:{dom}"
-        if key in tr:
-            traffic = tr[key]
+        rec = tr.get(f"{w['name']}:{dom}")
+        if rec and nblk == 64:
+            blob = b"".join(open(os.path.join(ROOT, s), "rb").read() for s in rec["sources"])
+            if hashlib.sha256(blob).hexdigest()[:16] == rec["sha256_16"]:
+                traffic = rec["bytes_per_launch"]  # else: the kernel changed since the capture
     hbm_total_bytes = 8.0 * nblk * (M * N + B * N)
     hbm_frac = (hbm_total_bytes / (statistics.mean(step_ms) / 1e3)) / (float(peaks["hbm_gbs"]) * 1e9)
 
