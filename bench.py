@@ -60,14 +60,38 @@ def flop_model(info) -> dict:
     Pg, Pr, Sr = info.P_gs, info.P_rec, info.S_rec
     gs = 6 * fft_flops(Pg) + 6.0 * 4 * Pg + 2.0 * Pg
     rec = (Sr + 1) * fft_flops(Pr) + 6.0 * (L + Sr * Pr + N) + 2.0 * (Sr - 1) * Pr
-    return {"czt_time": time_per_sensor * M, "czt_space": space_per_freq * L, "stage2_gs": (gs + rec) * B}
+    # Stage 2: GS + F_u for the FFT variants (the refinement step's transforms are not counted);
+    # 8 N L flops per beam-block (complex multiply-add) for the dense apply.
+    dense = info.stage2 >= 3
+    stage2 = 8.0 * N * L * B if dense else (gs + rec) * B
+    return {"czt_time": time_per_sensor * M, "czt_space": space_per_freq * L, "stage2": stage2}
 
 
-def alg_bytes(info) -> dict:
-    """Compulsory HBM bytes per block of each kernel (complex64 in + out, tables excluded)."""
+# Tensor-core variants: (planes of G and W, bytes per element, products per complex term, peak dtype).
+TC_VARIANTS = {4: (4, 2, 3, "bf16"), 5: (2, 4, 1, "tf32"), 6: (4, 4, 3, "tf32")}
+
+
+def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str) -> dict:
+    """Roofline entry of one kernel launch (nblk blocks) that took `ms` milliseconds."""
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    flops = flop_model(info)[kernel] * nblk
     M, N, B, L = info.M, info.N, info.B, info.L
-    return {"czt_time": 8.0 * (M * N + L * M), "czt_space": 8.0 * (L * M + B * L),
-            "stage2_gs": 8.0 * (B * L + B * N)}
+    if kernel == "stage2" and info.stage2 in TC_VARIANTS:
+        npl, esz, terms, dt = TC_VARIANTS[info.stage2]
+        nbytes = float(B) * npl * N * L * esz + 2.0 * B * L * nblk * 8 + B * N * nblk * 8.0
+        hbm = float(peaks["hbm_gbs"])
+        tc_peak = float(peaks["bf16_tflops"]) * (1.0 if dt == "bf16" else 0.5)  # nominal 2:1 bf16:tf32
+        if nbytes / (hbm * 1e9) >= terms * flops / (tc_peak * 1e12):
+            ach = nbytes / (ms / 1e3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": f"{peak_kind} hbm_gbs; bytes = G planes + W planes in/out + bhat"}
+        ach = terms * flops / (ms / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
+                "peak_source": f"{peak_kind} bf16_tflops x {'1' if dt == 'bf16' else '0.5 (tf32 nominal ratio)'}"}
+    ach = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+            "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)"}
 
 
 class ClockSampler:
@@ -290,7 +314,7 @@ def main() -> None:
         plan.toeplitz_apply(wbuf, out, nblk)
         ev[i][3].record(stream)
     torch.cuda.synchronize()
-    names = ["czt_time", "czt_space", "stage2_gs"]
+    names = ["czt_time", "czt_space", "stage2"]
     kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
 
     # End to end through the host-buffer entry point, pinned host memory, copies included.
@@ -317,21 +341,16 @@ def main() -> None:
         return
 
     peaks, peak_kind = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    flops = flop_model(info)
-    bytes_ = alg_bytes(info)
-    per_launch_flops = {"czt_time": flops["czt_time"] * nblk, "czt_space": flops["czt_space"] * nblk,
-                        "stage2_gs": flops["stage2_gs"] * nblk}
     dom = max(kern_ms, key=kern_ms.get)
-    achieved = per_launch_flops[dom] / (kern_ms[dom] / 1e3) / 1e12
+    roof = roofline(dom, info, nblk, kern_ms[dom], peaks, peak_kind)
+    s2name = fb.STAGE2_NAMES[info.stage2]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         import hashlib
         with open(tfile) as f:
             tr = json.load(f)
-        rec = tr.get(f"{w['name']}:{dom}")
+        rec = tr.get(f"{w['name']}:{dom}:{s2name}" if dom == "stage2" else f"{w['name']}:{dom}")
         if rec and nblk == 64:
             blob = b"".join(open(os.path.join(ROOT, s), "rb").read() for s in rec["sources"])
             if hashlib.sha256(blob).hexdigest()[:16] == rec["sha256_16"]:
@@ -359,11 +378,9 @@ def main() -> None:
         "rel_err_vs_oracle": rel_err,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "hbm_roofline_frac": hbm_frac,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": traffic,
-                     "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
-                                    f"({peak_kind} sm_max_mhz)"},
+        "roofline": dict(roof, kernel=dom, traffic=traffic),
         "kernels_ms": kern_ms,
+        "kernels_roofline": {k: roofline(k, info, nblk, v, peaks, peak_kind) for k, v in kern_ms.items()},
         "e2e": {"value": units * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},
         "gpu_launches": plan.launch_count(nblk) * args.steps,

@@ -62,7 +62,8 @@ enum fbst_stage2_kind {
   FBST_STAGE2_GS_IR1 = 2,      /* GS plus one FP32 refinement step beta += GS(w - A_b beta) */
   FBST_STAGE2_DENSE_FP32 = 3,  /* precomputed G_b = F_u A_b^{-1} (Sec. III-B), FP32 CUDA cores */
   FBST_STAGE2_DENSE_BF16X3 = 4,/* G_b on tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
-  FBST_STAGE2_DENSE_TF32 = 5   /* G_b on tensor cores in TF32, FP32 accumulate */
+  FBST_STAGE2_DENSE_TF32 = 5,  /* G_b on tensor cores in TF32, FP32 accumulate */
+  FBST_STAGE2_DENSE_TF32X3 = 6 /* G_b on tensor cores, split TF32 (hi*hi + hi*lo + lo*hi): FP32-class */
 };
 
 /* Array and beam grid. M = mx*my elements, B = bx*by beams. A linear array has my = by = 1. */
@@ -157,6 +158,11 @@ int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* str
 /* Stage 2 alone (Sec. V): w (device, [nblk][B][L]) -> bhat (device, [nblk][B][N]),
  * bhat_b = F_u (F_b^H F_b + delta I)^{-1} w_b, with the plan's stage-2 variant. */
 int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream);
+
+/* Synchronise `stream`, then return and clear the plan's device status word: FBST_OK, or the
+ * error a kernel recorded since the last check (FBST_ERR_TIMEOUT when a bounded device-side wait
+ * of the tensor-core kernel gave up; its outputs are then not valid). */
+int fbst_sync_status(fbst_plan_t p, void* stream);
 
 /* Copy the derived parameters of a plan. */
 int fbst_plan_info(fbst_plan_t p, fbst_info* out);

@@ -17,7 +17,8 @@ FBST_OK = 0
 STATUS_NAMES = {0: "FBST_OK", -1: "FBST_ERR_INVALID", -2: "FBST_ERR_OOM", -3: "FBST_ERR_CUDA",
                 -4: "FBST_ERR_UNSUPPORTED", -5: "FBST_ERR_TIMEOUT", -6: "FBST_ERR_NUMERIC"}
 ULA, URA = 0, 1
-STAGE2 = {"auto": 0, "gs": 1, "gs_ir1": 2, "dense_fp32": 3, "dense_bf16x3": 4, "dense_tf32": 5}
+STAGE2 = {"auto": 0, "gs": 1, "gs_ir1": 2, "dense_fp32": 3, "dense_bf16x3": 4, "dense_tf32": 5,
+          "dense_tf32x3": 6}
 STAGE2_NAMES = {v: k for k, v in STAGE2.items()}
 
 
@@ -67,6 +68,7 @@ SIGNATURES = {
     "fbst_czt_space": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_toeplitz_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_plan_info": (_I, [_VP, C.POINTER(Info)]),
+    "fbst_sync_status": (_I, [_VP, _VP]),
     "fbst_plan_generators": (_I, [_VP, _VP]),
     "fbst_destroy": (_I, [_VP]),
     "fbst_status_string": (C.c_char_p, [_I]),
@@ -191,6 +193,10 @@ class Plan:
     def toeplitz_apply(self, w, bhat, nblk: int, stream=None) -> None:
         """Stage 2: w [nblk][B][L] -> bhat [nblk][B][N]."""
         self._call("fbst_toeplitz_apply", w, bhat, nblk, stream)
+
+    def sync_status(self, stream=None) -> int:
+        """Synchronise the stream; return and clear the plan's device status word (0 = OK)."""
+        return int(self._lib.fbst_sync_status(self._h, _stream(stream)))
 
     def launch_count(self, nblk: int) -> int:
         return int(self._lib.fbst_launch_count(self._h, int(nblk)))

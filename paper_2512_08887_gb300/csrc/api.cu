@@ -47,7 +47,8 @@ static int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int n
     case FBST_STAGE2_GS_IR1: return launch_stage2_gs(p, w, bhat, nb, s);
     case FBST_STAGE2_DENSE_FP32: return launch_stage2_dense_fp32(p, w, bhat, nb, s);
     case FBST_STAGE2_DENSE_BF16X3:
-    case FBST_STAGE2_DENSE_TF32: return launch_stage2_dense_tc(p, w, bhat, nb, s);
+    case FBST_STAGE2_DENSE_TF32:
+    case FBST_STAGE2_DENSE_TF32X3: return launch_stage2_dense_tc(p, w, bhat, nb, s);
     default: return FBST_ERR_INVALID;
   }
 }
@@ -162,6 +163,16 @@ int fbst_destroy(fbst_plan_t p) {
   free_plan_memory(p);
   delete p;
   return FBST_OK;
+}
+
+int fbst_sync_status(fbst_plan_t p, void* stream) {
+  if (!p) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FBST_CUDA_TRY(cudaStreamSynchronize(s));
+  int st = 0;
+  FBST_CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) FBST_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
+  return st;
 }
 
 int fbst_plan_info(fbst_plan_t p, fbst_info* out) {

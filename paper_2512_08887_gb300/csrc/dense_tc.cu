@@ -1,12 +1,484 @@
-// Dense stage-2 apply on the tensor cores (placeholder until the tcgen05 kernel lands).
+// Dense stage 2 on the tensor cores (Sec. III-B "precompute" variant, Table I): for every beam b
+//   bhat_b[:, blk] = G_b w_b[blk],   G_b = F_u A_b^{-1}  (N x L complex, built in FP64 at plan time).
+//
+// Per beam the blocks form the right-hand sides of a complex GEMM (N x L) . (L x nblk). It runs as
+// four real products on split real/imaginary planes, so neither operand is duplicated:
+//   C_re = G_re W_re - G_im W_im,   C_im = G_re W_im + G_im W_re,
+// the subtraction done by the negate-B bit of the MMA instruction descriptor. Precision variants:
+//   BF16X3 : G = G_hi + G_lo, W = W_hi + W_lo in BF16; hi*hi + hi*lo + lo*hi per product (kind::f16)
+//   TF32   : G, W rounded to TF32, one product (kind::tf32)
+//   TF32X3 : G = G_hi + G_lo, W = W_hi + W_lo with TF32 hi parts and FP32 residuals (kind::tf32),
+//            hi*hi + hi*lo + lo*hi: FP32-class accuracy
+// always with FP32 accumulation in tensor memory.
+//
+// Kernel structure (one CTA = one beam x 128 output samples x up to NB blocks, 128 threads):
+//   thread 0  : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, one mbarrier per stage)
+//   thread 32 : MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = NB, K = 32 bytes per step)
+//   warp 1    : tensor-memory allocation / release (2 accumulators x NB columns)
+//   warps 0-3 : epilogue (tcgen05.ld 32x32b, rows = samples, coalesced complex64 stores)
+// Every mbarrier wait is bounded by %globaltimer; on timeout the kernel records FBST_ERR_TIMEOUT
+// in the plan's status word, waits (bounded) for its copies in flight, frees its tensor memory
+// and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fbst {
 
-int build_dense_tc_operand(fbst_plan_s*, cudaStream_t) { return FBST_ERR_UNSUPPORTED; }
+enum tc_variant { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2 };
 
-int launch_stage2_dense_tc(const fbst_plan_s*, const float2*, float2*, int, cudaStream_t) {
-  return FBST_ERR_UNSUPPORTED;
+template <int V> struct tc_traits;
+template <> struct tc_traits<TC_BF16X3> {
+  static constexpr int ESZ = 2, NPL = 4, TERMS = 3, MAX_NB = 64, STAGES = 2;
+  static constexpr uint32_t FMT = 1;  // BF16
+};
+template <> struct tc_traits<TC_TF32> {
+  static constexpr int ESZ = 4, NPL = 2, TERMS = 1, MAX_NB = 128, STAGES = 3;
+  static constexpr uint32_t FMT = 2;  // TF32
+};
+template <> struct tc_traits<TC_TF32X3> {
+  static constexpr int ESZ = 4, NPL = 4, TERMS = 3, MAX_NB = 64, STAGES = 2;
+  static constexpr uint32_t FMT = 2;  // TF32
+};
+
+static int variant_of(int stage2) {
+  switch (stage2) {
+    case FBST_STAGE2_DENSE_BF16X3: return TC_BF16X3;
+    case FBST_STAGE2_DENSE_TF32: return TC_TF32;
+    case FBST_STAGE2_DENSE_TF32X3: return TC_TF32X3;
+    default: return -1;
+  }
+}
+
+constexpr int kRowBytes = 128;    // one K-chunk row (the 128-byte swizzle span)
+constexpr int kTileM = 128;       // output samples per CTA (MMA M)
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait
+
+// ---------------------------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it did not complete within kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout written by TMA:
+// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, optional negation of B, both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int M, int N, bool neg_b) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((neg_b ? 1u : 0u) << 14) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int V>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if constexpr (V == TC_BF16X3) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Operand preparation
+// ---------------------------------------------------------------------------------------------
+// Split one FP32 value into the variant's planes (hi, lo) or (rounded).
+template <int V>
+__device__ __forceinline__ void split_store(void* base, size_t plane_stride, size_t idx, int comp, float x) {
+  if constexpr (V == TC_BF16X3) {
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    p[(size_t)(2 * comp) * plane_stride + idx] = hi;
+    p[(size_t)(2 * comp + 1) * plane_stride + idx] = lo;
+  } else if constexpr (V == TC_TF32) {
+    static_cast<float*>(base)[(size_t)comp * plane_stride + idx] = round_tf32(x);
+  } else {
+    const float hi = round_tf32(x);
+    static_cast<float*>(base)[(size_t)(2 * comp) * plane_stride + idx] = hi;
+    static_cast<float*>(base)[(size_t)(2 * comp + 1) * plane_stride + idx] = x - hi;
+  }
+}
+
+// G [B][N][L] complex64 -> planes [B][NPL][N][L].
+template <int V>
+__global__ void k_tc_split_G(const float2* __restrict__ G, void* __restrict__ out, int B, int N, int L) {
+  constexpr int NPL = tc_traits<V>::NPL;
+  const size_t per_beam = (size_t)N * L;
+  const size_t total = (size_t)B * per_beam;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / per_beam, r = i % per_beam;
+    const float2 g = G[i];
+    char* beam = static_cast<char*>(out) + b * NPL * per_beam * tc_traits<V>::ESZ;
+    split_store<V>(beam, per_beam, r, 0, g.x);
+    split_store<V>(beam, per_beam, r, 1, g.y);
+  }
+}
+
+// w [nblk][B][L] complex64 -> planes [B][NPL][NBW][L]; rows nblk..nrows-1 are zero.
+template <int V>
+__global__ void k_tc_prep_w(const float2* __restrict__ w, void* __restrict__ out, int B, int L, int nblk, int nrows,
+                            int NBW) {
+  constexpr int NPL = tc_traits<V>::NPL;
+  const int b = blockIdx.y;
+  const size_t plane = (size_t)NBW * L;
+  char* beam = static_cast<char*>(out) + (size_t)b * NPL * plane * tc_traits<V>::ESZ;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows * L; i += gridDim.x * blockDim.x) {
+    const int blk = i / L, l = i % L;
+    const float2 v = blk < nblk ? w[((size_t)blk * B + b) * L + l] : make_float2(0.f, 0.f);
+    split_store<V>(beam, plane, (size_t)blk * L + l, 0, v.x);
+    split_store<V>(beam, plane, (size_t)blk * L + l, 1, v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The GEMM kernel
+// ---------------------------------------------------------------------------------------------
+template <int V, int NB>
+struct tc_smem {
+  static constexpr int NPL = tc_traits<V>::NPL;
+  static constexpr int STAGES = tc_traits<V>::STAGES;
+  static constexpr int A_TILE = kTileM * kRowBytes;   // one plane
+  static constexpr int B_TILE = NB * kRowBytes;
+  static constexpr int STAGE_BYTES = NPL * (A_TILE + B_TILE);
+  static constexpr int BYTES = STAGES * STAGE_BYTES + 1024 /* alignment slack */ + 256 /* barriers */;
+};
+
+template <int V, int NB>
+__global__ void __launch_bounds__(128, 1)
+k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+           float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
+  using TR = tc_traits<V>;
+  using SM = tc_smem<V, NB>;
+  constexpr int NPL = TR::NPL, STAGES = TR::STAGES;
+  constexpr int KELEM = kRowBytes / TR::ESZ;      // elements per K-chunk row
+  constexpr int KSTEPS = kRowBytes / 32;          // MMAs of 32 bytes of K per chunk
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * SM::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTileM, b = blockIdx.y, blk0 = blockIdx.z * NB;
+  const int nchunks = (L + KELEM - 1) / KELEM;
+  constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : (2 * NB <= 64 ? 64 : (2 * NB <= 128 ? 128 : 256));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES;
+      if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) {
+        atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * SM::STAGE_BYTES;
+      mbar_expect_tx(&full[s], SM::STAGE_BYTES);
+      for (int pl = 0; pl < NPL; ++pl) {
+        tma_load_3d(st + pl * SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * NPL + pl);
+        tma_load_3d(st + NPL * SM::A_TILE + pl * SM::B_TILE, &mapB, &full[s], c * KELEM, blk0, b * NPL + pl);
+      }
+      issued = c + 1;
+    }
+    // Copies still in flight must land before the CTA can leave.
+    if (*abort_flag) {
+      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+        (void)mbar_wait(&full[c % STAGES], (c / STAGES) & 1);
+    }
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t ID_POS = make_idesc(TR::FMT, kTileM, NB, false);
+    constexpr uint32_t ID_NEG = make_idesc(TR::FMT, kTileM, NB, true);
+    const uint32_t d_re = tmem, d_im = tmem + NB;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c % STAGES;
+      if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
+        atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * SM::STAGE_BYTES);
+      // Planes: TERMS == 1 -> {re, im}; TERMS == 3 -> {re_hi, re_lo, im_hi, im_lo}.
+      constexpr int RE_HI = 0, RE_LO = (TR::TERMS == 3 ? 1 : 0), IM_HI = (TR::TERMS == 3 ? 2 : 1),
+                    IM_LO = (TR::TERMS == 3 ? 3 : 1);
+#pragma unroll
+      for (int k = 0; k < KSTEPS; ++k) {
+        auto da = [&](int pl) { return smem_desc_sw128(st + pl * SM::A_TILE + k * 32); };
+        auto db = [&](int pl) { return smem_desc_sw128(st + NPL * SM::A_TILE + pl * SM::B_TILE + k * 32); };
+        const uint32_t acc0 = (c > 0 || k > 0) ? 1u : 0u;
+        // C_re = G_re W_re - G_im W_im ; C_im = G_re W_im + G_im W_re
+        mma_issue<V>(d_re, da(RE_HI), db(RE_HI), ID_POS, acc0);
+        mma_issue<V>(d_re, da(IM_HI), db(IM_HI), ID_NEG, 1u);
+        mma_issue<V>(d_im, da(RE_HI), db(IM_HI), ID_POS, acc0);
+        mma_issue<V>(d_im, da(IM_HI), db(RE_HI), ID_POS, 1u);
+        if constexpr (TR::TERMS == 3) {
+          mma_issue<V>(d_re, da(RE_HI), db(RE_LO), ID_POS, 1u);
+          mma_issue<V>(d_re, da(RE_LO), db(RE_HI), ID_POS, 1u);
+          mma_issue<V>(d_re, da(IM_HI), db(IM_LO), ID_NEG, 1u);
+          mma_issue<V>(d_re, da(IM_LO), db(IM_HI), ID_NEG, 1u);
+          mma_issue<V>(d_im, da(RE_HI), db(IM_LO), ID_POS, 1u);
+          mma_issue<V>(d_im, da(RE_LO), db(IM_HI), ID_POS, 1u);
+          mma_issue<V>(d_im, da(IM_HI), db(RE_LO), ID_POS, 1u);
+          mma_issue<V>(d_im, da(IM_LO), db(RE_HI), ID_POS, 1u);
+        }
+      }
+      mma_commit(&empty[s]);  // this stage's smem may be refilled once these MMAs have read it
+    }
+    mma_commit(done);  // all issued MMAs complete -> accumulators final
+  }
+  __syncwarp();
+
+  // ---------------- Epilogue: all four warps ----------------
+  const bool have = mbar_wait(done, 0);
+  if (!have) {
+    if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
+  } else if (!*abort_flag) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int n = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int j0 = 0; j0 < NB; j0 += 16) {
+      float re[16], im[16];
+      tmem_ld16(lane_base + j0, re);
+      tmem_ld16(lane_base + NB + j0, im);
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int blk = blk0 + j0 + jj;
+        if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj], im[jj]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D map over planes [Z][Y][X] (X contiguous, ESZ-byte elements), box {128 bytes of X, boxY, 1},
+// 128-byte swizzle; out-of-range elements read as zero.
+static int make_map(CUtensorMap* map, const void* base, int esz, uint64_t X, uint64_t Y, uint64_t Z, uint32_t boxY) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return FBST_ERR_UNSUPPORTED;
+  const cuuint64_t dims[3] = {X, Y, Z};
+  const cuuint64_t strides[2] = {X * esz, X * Y * esz};
+  const cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), boxY, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? FBST_OK : FBST_ERR_CUDA;
+}
+
+template <int V>
+static size_t plane_bytes_G(const fbst_info& in) {
+  return (size_t)in.B * tc_traits<V>::NPL * in.N * in.L * tc_traits<V>::ESZ;
+}
+
+static int round16(int x) { return (x + 15) / 16 * 16; }
+
+template <int V>
+static int build_operand_V(fbst_plan_s* p, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  if (in.L % 8 != 0) return FBST_ERR_UNSUPPORTED;  // 16-byte rows for TMA
+  const size_t bytes = plane_bytes_G<V>(in);
+  FBST_CUDA_TRY(cudaMalloc(&p->Gtc, bytes));
+  p->Gtc_bytes = bytes;
+  k_tc_split_G<V><<<4096, 256, 0, s>>>(p->G, p->Gtc, in.B, in.N, in.L);
+  FBST_CUDA_TRY(cudaGetLastError());
+  const int NBW = round16(p->band.max_blocks);
+  p->ws_tc_bytes = (size_t)in.B * tc_traits<V>::NPL * NBW * in.L * tc_traits<V>::ESZ;
+  FBST_CUDA_TRY(cudaMalloc(&p->ws_tc, p->ws_tc_bytes));
+  FBST_CUDA_TRY(cudaMemsetAsync(p->ws_tc, 0, p->ws_tc_bytes, s));
+  return FBST_OK;
+}
+
+int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s) {
+  if (!tensor_map_encoder()) return FBST_ERR_UNSUPPORTED;
+  switch (variant_of(p->info.stage2)) {
+    case TC_BF16X3: return build_operand_V<TC_BF16X3>(p, s);
+    case TC_TF32: return build_operand_V<TC_TF32>(p, s);
+    case TC_TF32X3: return build_operand_V<TC_TF32X3>(p, s);
+    default: return FBST_ERR_INVALID;
+  }
+}
+
+template <int V, int NB>
+static int gemm_NB(const fbst_plan_s* p, float2* bhat, int nblk, cudaStream_t s) {
+  using TR = tc_traits<V>;
+  const fbst_info& in = p->info;
+  const int NBW = round16(p->band.max_blocks);
+  CUtensorMap mapA, mapB;
+  int r = make_map(&mapA, p->Gtc, TR::ESZ, in.L, in.N, (uint64_t)in.B * TR::NPL, kTileM);
+  if (r != FBST_OK) return r;
+  r = make_map(&mapB, p->ws_tc, TR::ESZ, in.L, NBW, (uint64_t)in.B * TR::NPL, NB);
+  if (r != FBST_OK) return r;
+  const int smem = tc_smem<V, NB>::BYTES;
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc<V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const dim3 grid((in.N + kTileM - 1) / kTileM, in.B, (nblk + NB - 1) / NB);
+  k_dense_tc<V, NB><<<grid, 128, smem, s>>>(mapA, mapB, bhat, in.B, in.N, in.L, nblk, p->d_status);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+template <int V>
+static int launch_V(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  using TR = tc_traits<V>;
+  const fbst_info& in = p->info;
+  const int NBW = round16(p->band.max_blocks);
+  const int nrows = round16(nblk);
+  if (nrows > NBW) return FBST_ERR_INVALID;
+  k_tc_prep_w<V><<<dim3(std::min(64, (nrows * in.L + 255) / 256), in.B), 256, 0, s>>>(w, p->ws_tc, in.B, in.L, nblk,
+                                                                                     nrows, NBW);
+  FBST_CUDA_TRY(cudaGetLastError());
+  // Smallest MMA width that covers the blocks (16..MAX_NB in steps of 16).
+  const int want = std::min(nrows, TR::MAX_NB);
+  if (want <= 16) return gemm_NB<V, 16>(p, bhat, nblk, s);
+  if (want <= 32) return gemm_NB<V, 32>(p, bhat, nblk, s);
+  if (want <= 64) return gemm_NB<V, 64>(p, bhat, nblk, s);
+  if constexpr (TR::MAX_NB >= 128) return gemm_NB<V, 128>(p, bhat, nblk, s);
+  return FBST_ERR_INVALID;
+}
+
+int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  if (nblk <= 0) return FBST_OK;
+  if (!p->Gtc || !p->ws_tc) return FBST_ERR_INVALID;
+  switch (variant_of(p->info.stage2)) {
+    case TC_BF16X3: return launch_V<TC_BF16X3>(p, w, bhat, nblk, s);
+    case TC_TF32: return launch_V<TC_TF32>(p, w, bhat, nblk, s);
+    case TC_TF32X3: return launch_V<TC_TF32X3>(p, w, bhat, nblk, s);
+    default: return FBST_ERR_INVALID;
+  }
 }
 
 }  // namespace fbst

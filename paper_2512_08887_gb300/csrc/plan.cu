@@ -90,7 +90,7 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
   if (band->max_blocks < 1) return FBST_ERR_INVALID;
   switch (band->stage2) {
     case FBST_STAGE2_AUTO: case FBST_STAGE2_GS: case FBST_STAGE2_GS_IR1: case FBST_STAGE2_DENSE_FP32:
-    case FBST_STAGE2_DENSE_BF16X3: case FBST_STAGE2_DENSE_TF32: break;
+    case FBST_STAGE2_DENSE_BF16X3: case FBST_STAGE2_DENSE_TF32: case FBST_STAGE2_DENSE_TF32X3: break;
     default: return FBST_ERR_INVALID;
   }
   const int L = (int)L64;

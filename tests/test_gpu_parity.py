@@ -189,3 +189,43 @@ def test_on_grid_plane_wave_is_reproduced_on_gpu():
     y = array_record(pb.geom, [src], 0.5, 64, None, None)[None].astype(np.complex64)
     got = run(plan, "execute", y, (1, 32, 64), 1)
     assert O.rel_l2(got[0, b], waveform(src, np.arange(64))) < 1e-2
+
+
+TC_TOL = {"dense_tf32x3": TOL_E2E, "dense_bf16x3": 1e-3, "dense_tf32": 3e-2}
+
+
+@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_bf16x3", "dense_tf32"])
+@pytest.mark.parametrize("case", [("ula", 16, 1, 16, 1, 64, 0.5, 3), ("ula", 13, 1, 10, 1, 24, 0.37, 5),
+                                  ("ura", 8, 8, 8, 8, 64, 0.3, 2), ("ula", 48, 1, 40, 1, 256, 0.5, 70)])
+def test_dense_tensor_core_matches_oracle(rng, stage2, case):
+    # Tensor-core dense apply (tcgen05, TMA, TMEM). The last case has 70 blocks: two block groups
+    # and 2N/128 = 4 row tiles; the first ones have N < 128 (row tiles partly outside G_b).
+    kind, mx, my, bx, by, N, fbw, nblk = case
+    plan, pb = make(kind, mx, my, bx, by, N, fbw, stage2=stage2, max_blocks=nblk)
+    y = crandn(rng, nblk, pb.M, N)
+    w = O.fan_coefficients(pb, y).astype(np.complex64)
+    got = run(plan, "toeplitz_apply", w, (nblk, pb.B, N), nblk)
+    assert plan.sync_status() == 0
+    ref = O.Stage2Factors(pb).apply(w)
+    err = O.rel_l2(got, ref)
+    assert err < TC_TOL[stage2], f"{stage2}: {err:.3e}"
+
+
+def test_execute_c3_precision_split_sampled_beams():
+    # Config C3: URA 32x32, N = 512, B = 32x32, fb = 0.3; stage 2 on the tensor cores, each variant's
+    # error against the FP64 oracle printed. Bars: 1e-3 for the tensor-core path; TF32x3 is also
+    # held to 5e-5 (FP32 CUDA-core stage 2 reaches ~1e-6 here; TF32x3 drops lo*lo and accumulates
+    # in the tensor pipe) and plain TF32 to 3e-2.
+    d = configs.config_data("C3", nblk=4, Q=64)
+    beams = np.array([0, 33, 500, 777, 1023])
+    errs, ref = {}, None
+    for stage2 in ("dense_tf32x3", "dense_bf16x3", "dense_tf32"):
+        plan, pb = make("ura", 32, 32, 32, 32, 512, 0.3, stage2=stage2, max_blocks=4)
+        got = run(plan, "execute", d["y"], (4, 1024, 512), 4)
+        assert plan.sync_status() == 0
+        if ref is None:
+            ref = O.fbst(pb, d["y"], beams=beams)
+        errs[stage2] = O.rel_l2(got[:, beams], ref)
+        plan.close()
+    print("C3 rel L2 error vs FP64 oracle:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["dense_tf32x3"] < 5e-5 and errs["dense_bf16x3"] < 1e-3 and errs["dense_tf32"] < 3e-2, errs
