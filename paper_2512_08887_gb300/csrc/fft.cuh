@@ -109,11 +109,20 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
       const int k = j & (NS - 1);                  // position inside the current sub-transform
       V w[R];
       if constexpr (NS > 1) {
+        // Load the powers w^1, w^2, w^4, w^8 of the pass twiddle and form the others as products
+        // of at most three of them (L1 traffic of log2(R) loads instead of R-1).
 #pragma unroll
-        for (int s = 1; s < R; ++s) {
+        for (int s = 1; s < R; s <<= 1) {
           V ws = tw[s * k * TW_STRIDE];
           if constexpr (DIR > 0) ws.y = -ws.y;
           w[s] = ws;
+        }
+#pragma unroll
+        for (int s = 3; s < R; ++s) {
+          if ((s & (s - 1)) != 0) {
+            const int hi = 1 << (31 - __clz(s));
+            w[s] = cmul(w[hi], w[s - hi]);
+          }
         }
       }
       const int base = (j - k) * R + k;

@@ -31,20 +31,26 @@ k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float
   constexpr int SBG = fft_smem_elems<float2>(PG);
   extern __shared__ float2 sm[];
   float2* beta_s = sm + 2 * SBG;  // [L]
-  const int b = blockIdx.x, t = threadIdx.x;
-  const int blk0 = blockIdx.y * blk_per_cta;
-  const int blk1 = min(nblk, blk0 + blk_per_cta);
+  const int t = threadIdx.x;
   const int Lr = L / SR;
-
+  // Work item = (beam, block), beam-major; CTA c owns the contiguous range [c*I/G, (c+1)*I/G) of
+  // the I = B*nblk items and keeps the current beam's spectra in registers.
+  const long long items = (long long)B * nblk;
+  const long long it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+  int b = -1;
   float2 X[EG], Vv[EG];
-  const float2* xv = XV + (size_t)b * 2 * PG;
-#pragma unroll
-  for (int r = 0; r < EG; ++r) {
-    X[r] = xv[t + T * r];
-    Vv[r] = xv[PG + t + T * r];
-  }
 
-  for (int blk = blk0; blk < blk1; ++blk) {
+  for (long long it = it0; it < it1; ++it) {
+    const int blk = (int)(it % nblk);
+    if ((int)(it / nblk) != b) {
+      b = (int)(it / nblk);
+      const float2* xv = XV + (size_t)b * 2 * PG;
+#pragma unroll
+      for (int r = 0; r < EG; ++r) {
+        X[r] = xv[t + T * r];
+        Vv[r] = xv[PG + t + T * r];
+      }
+    }
     const float2* wb = w + ((size_t)blk * B + b) * L;
     float2 v[EG];
 #pragma unroll
@@ -110,11 +116,6 @@ k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float
   }
 }
 
-static int blocks_per_cta(int nblk, int ctas_per_block_set, int target) {
-  int chunks = std::max(1, std::min(nblk, (target + ctas_per_block_set - 1) / std::max(1, ctas_per_block_set)));
-  return (nblk + chunks - 1) / chunks;
-}
-
 template <int PG, int PR, int SR, bool IR>
 static int stage2_gs_P(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
   constexpr int EG = gs_e<PG>::value;
@@ -122,10 +123,14 @@ static int stage2_gs_P(const fbst_plan_s* p, const float2* w, float2* bhat, int 
   const fbst_info& in = p->info;
   const size_t smem = sizeof(float2) * (2 * (size_t)fft_smem_elems<float2>(PG) + in.L);
   FBST_CUDA_TRY(cudaFuncSetAttribute(k_stage2_gs<PG, PR, SR, IR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int bpc = blocks_per_cta(nblk, in.B, 8 * 152);
-  const dim3 grid(in.B, (nblk + bpc - 1) / bpc);
+  int dev = 0, sms = 0, per_sm = 0;
+  FBST_CUDA_TRY(cudaGetDevice(&dev));
+  FBST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FBST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage2_gs<PG, PR, SR, IR>, T, smem));
+  const long long items = (long long)in.B * nblk;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(items, (long long)sms * std::max(1, per_sm)));
   k_stage2_gs<PG, PR, SR, IR><<<grid, T, smem, s>>>(w, bhat, p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, p->tw32,
-                                                in.B, in.L, in.N, nblk, bpc);
+                                                in.B, in.L, in.N, nblk, 0);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
