@@ -184,6 +184,48 @@ const char* fbst_last_error(void);
 /* Number of kernels one fbst_execute of nblk blocks launches (for launch accounting). */
 int fbst_launch_count(fbst_plan_t p, int nblk);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches of independent arrays. Blocks, requests and whole arrays are independent (Sec. III-A
+ * streaming remark; Sec. VI on parallel execution over beams and frequency pairs), so many plans of
+ * different sizes can run together. A batch run groups the plans' work by kernel and transform
+ * size into a few launches that spread all their work items over the whole GPU, and replays that
+ * launch sequence as a CUDA graph.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fbst_batch_s* fbst_batch_t;
+
+/* Group `count` distinct plans into a batch (the batch keeps pointers; the plans must outlive
+ * it and must not run elsewhere while a batch run using them is in flight). */
+int fbst_batch_create(fbst_batch_t* out, const fbst_plan_t* plans, int count);
+
+/* Run plan i on nblk[i] blocks (0 <= nblk[i] <= that plan's max_blocks): y[i] ([nblk][M][N]) ->
+ * bhat[i] ([nblk][B][N]), device pointers, asynchronous on `stream`. The first run with a given
+ * set of pointers and block counts launches eagerly and captures the launch sequence into a CUDA
+ * graph; later runs with the same arguments replay the graph. Results equal per-plan fbst_execute. */
+int fbst_batch_execute(fbst_batch_t b, const void* const* y, void* const* bhat, const int* nblk, void* stream);
+
+/* Kernels in one graph replay of the batch (0 before the first run). */
+int fbst_batch_launch_count(fbst_batch_t b);
+
+/* Release the batch (not its plans). */
+int fbst_batch_destroy(fbst_batch_t b);
+
+/* ---------------------------------------------------------------------------------------------
+ * Launch shapes of the two stage-1 kernels: the Stockham radix (elements per thread, E) and the
+ * transforms per CTA (G). Not part of the method; performance only, results stay within rounding.
+ * ------------------------------------------------------------------------------------------- */
+/* Time every compiled shape of the temporal and the spatial chirp-z kernels for this plan on
+ * nblk blocks (on the plan's workspace and a temporary input buffer it allocates), keep the
+ * fastest in the plan, and write {time_E, time_G, space_E, space_G} to shapes4 (may be NULL).
+ * Synchronises `stream`. Not allowed during stream capture. */
+int fbst_autotune(fbst_plan_t p, int nblk, void* stream, int* shapes4);
+
+/* Set the shapes explicitly ({0, 0} restores the built-in default for that kernel);
+ * FBST_ERR_UNSUPPORTED if no kernel of that shape is compiled for the plan's transform size. */
+int fbst_set_shapes(fbst_plan_t p, int time_E, int time_G, int space_E, int space_G);
+
+/* Read the shapes in use: {time_E, time_G, space_E, space_G}. */
+int fbst_get_shapes(fbst_plan_t p, int* shapes4);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,6 +2,7 @@
 from ._native import (  # noqa: F401
     FBSTError,
     Band,
+    Batch,
     Geometry,
     Info,
     Plan,

@@ -74,6 +74,13 @@ SIGNATURES = {
     "fbst_status_string": (C.c_char_p, [_I]),
     "fbst_last_error": (C.c_char_p, []),
     "fbst_launch_count": (_I, [_VP, _I]),
+    "fbst_batch_create": (_I, [C.POINTER(_VP), C.POINTER(_VP), _I]),
+    "fbst_batch_execute": (_I, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_I), _VP]),
+    "fbst_batch_launch_count": (_I, [_VP]),
+    "fbst_batch_destroy": (_I, [_VP]),
+    "fbst_autotune": (_I, [_VP, _I, _VP, C.POINTER(_I)]),
+    "fbst_set_shapes": (_I, [_VP, _I, _I, _I, _I]),
+    "fbst_get_shapes": (_I, [_VP, C.POINTER(_I)]),
 }
 
 _lib = None
@@ -201,6 +208,20 @@ class Plan:
     def launch_count(self, nblk: int) -> int:
         return int(self._lib.fbst_launch_count(self._h, int(nblk)))
 
+    def autotune(self, nblk: int, stream=None) -> tuple:
+        """Time every compiled stage-1 launch shape on nblk blocks; keep and return the fastest."""
+        out = (C.c_int * 4)()
+        _check(self._lib.fbst_autotune(self._h, int(nblk), _stream(stream), out), "fbst_autotune")
+        return tuple(out)
+
+    def set_shapes(self, time_E: int, time_G: int, space_E: int, space_G: int) -> None:
+        _check(self._lib.fbst_set_shapes(self._h, time_E, time_G, space_E, space_G), "fbst_set_shapes")
+
+    def shapes(self) -> tuple:
+        out = (C.c_int * 4)()
+        _check(self._lib.fbst_get_shapes(self._h, out), "fbst_get_shapes")
+        return tuple(out)
+
     def generators(self):
         """First column of every A_b^{-1} from the FP64 Levinson solve, numpy complex128 [B][L]."""
         import numpy as np
@@ -224,3 +245,36 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Independent plans run together as grouped launches replayed from a CUDA graph."""
+
+    def __init__(self, plans):
+        self._lib = load_library()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = C.c_void_p()
+        _check(self._lib.fbst_batch_create(C.byref(h), arr, len(self.plans)), "fbst_batch_create")
+        self._h = h
+
+    def execute(self, ys, bhats, nblks, stream=None) -> None:
+        n = len(self.plans)
+        ya = (C.c_void_p * n)(*[_ptr(v) for v in ys])
+        ba = (C.c_void_p * n)(*[_ptr(v) for v in bhats])
+        na = (C.c_int * n)(*[int(v) for v in nblks])
+        _check(self._lib.fbst_batch_execute(self._h, ya, ba, na, _stream(stream)), "fbst_batch_execute")
+
+    def launch_count(self) -> int:
+        return int(self._lib.fbst_batch_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fbst_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -37,6 +37,61 @@ constexpr int kTwiddleSize = 4096;
 }  // namespace fbst
 
 // ---------------------------------------------------------------------------------------------
+// Jobs: one plan's share of a stage launch. A launch takes up to kMaxJobs jobs of the same
+// transform size and shape (passed by value as a __grid_constant__ parameter), flattens their
+// work items and splits them evenly over the resident CTAs. A single-plan call is a one-job launch;
+// a batch of uneven arrays groups its plans' jobs by transform size.
+// ---------------------------------------------------------------------------------------------
+namespace fbst {
+constexpr int kMaxJobs = 32;
+
+struct time_job {      // temporal chirp-z of one plan over nblk blocks
+  const float2* y;
+  float2* yhat;
+  const float2* pre;
+  const float2* gspec;
+  const float2* post;
+  int M, N, L, S, nblk;
+  long long first;     // first flattened work item of this job
+};
+
+struct space_job {     // spatial chirp-z (linear array) of one plan over nblk blocks
+  const float2* yhat;
+  float2* w;
+  const float2* pre;
+  const float2* kspec;
+  const float2* post;
+  int M, B, L, nblk;
+  long long first;
+};
+
+struct gs_job {        // Gohberg-Semencul stage 2 + reconstruction of one plan over nblk blocks
+  const float2* w;
+  float2* bhat;
+  const float2* XV;
+  const float2* Aspec;
+  const float2* pre_r;
+  const float2* qspec;
+  const float2* post_r;
+  int B, L, N, nblk;
+  long long first;
+};
+
+template <typename J>
+struct job_list {
+  J job[kMaxJobs];
+  int n;
+  long long total;     // total work items over all jobs
+};
+
+// Launch shape of a Stockham kernel: elements per thread (the radix) and transforms per CTA.
+struct fft_shape {
+  int E;
+  int G;
+};
+}  // namespace fbst
+
+// ---------------------------------------------------------------------------------------------
 // The plan. All pointers are device memory owned by the plan unless stated otherwise.
 // ---------------------------------------------------------------------------------------------
 struct fbst_axis_tables {
@@ -93,6 +148,11 @@ struct fbst_plan_s {
   float2* stage_bhat;  // [max_blocks][B][N]
 
   int* d_status;       // device status word (FP64 plan kernels report here)
+
+  // Launch shapes of the temporal and spatial chirp-z kernels ({0, 0} = built-in default;
+  // fbst_autotune / fbst_set_shapes change them).
+  fbst::fft_shape shape_time;
+  fbst::fft_shape shape_space;
 };
 
 #define FBST_CUDA_TRY(expr)                                  \
@@ -111,6 +171,27 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk, cudaStream_t s);
 int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s);
 int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+
+// Multi-job launchers: every job of `jl` shares the transform size P (and for stage 2 the
+// reconstruction size/splits and the refinement flag).
+int launch_time_jobs(const job_list<time_job>& jl, int P, fft_shape shape, int max_Lh, const float2* tw,
+                     cudaStream_t s);
+int launch_space_jobs(const job_list<space_job>& jl, int P, fft_shape shape, int max_B, const float2* tw,
+                      cudaStream_t s);
+int launch_gs_jobs(const job_list<gs_job>& jl, int PG, int PR, int SR, bool IR, int max_L, const float2* tw,
+                   cudaStream_t s);
+// Job of one plan for nblk blocks (first = 0), and the shape the plan uses for it.
+time_job make_time_job(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk);
+space_job make_space_job(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk);
+gs_job make_gs_job(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk);
+fft_shape time_shape(const fbst_plan_s* p);
+fft_shape space_shape(const fbst_plan_s* p);
+// Shapes that have a compiled kernel for transform size P (fills up to `cap` entries).
+int time_shapes(int P, fft_shape* out, int cap);
+int space_shapes(int P, fft_shape* out, int cap);
+// Work items of a job (for the flattened ranges) given the launch shape.
+long long time_items(const time_job& j, fft_shape sh, int P);
+long long space_items(const space_job& j, fft_shape sh, int P);
 int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 int stage2_launches(const fbst_plan_s* p);

@@ -1,0 +1,252 @@
+// Spatial chirp-z of stage 1 (Sec. IV, the sum over elements; App. B for rectangular arrays):
+//   w[b, ell] = sum_m yhat[m, ell] exp(2*pi*i*kappa_ell*(u_b.p_m)),  kappa_ell = rho*(1/fb + eps*ell'/L),
+// one Bluestein chirp-z per frequency with a frequency-dependent chirp rate (tables from plan.cu).
+// Layout yhat [blk][L][M] -> w [blk][B][L]: a work item is G consecutive frequencies of one block;
+// the transpose goes through shared memory and leaves as G-frequency runs (32-byte sectors).
+// Work items are tile-major, so a CTA's contiguous range mostly stays on one frequency tile and
+// keeps that tile's chirps and kernel spectrum in registers.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "launch_util.cuh"
+
+namespace fbst {
+
+template <int P, int E, int G>
+__global__ void __launch_bounds__(G * (P / E))
+k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __restrict__ tw) {
+  constexpr int T = P / E;
+  constexpr int SB = fft_smem_elems<float2>(P);
+  extern __shared__ float2 sm[];
+  const int g = threadIdx.x / T, t = threadIdx.x % T;
+  float2* fbuf = sm + g * SB;
+  float2* tile = sm + G * SB;  // [B][G]
+  long long it0, it1;
+  my_range(jl.total, &it0, &it1);
+  int j = 0, cur_j = -1, cur_lt = -1;
+  float2 pr[E], ks[E], po[E];
+  for (long long it = it0; it < it1; ++it) {
+    while (j + 1 < jl.n && jl.job[j + 1].first <= it) ++j;
+    const space_job& J = jl.job[j];
+    const int M = J.M, B = J.B, L = J.L, nblk = J.nblk;
+    const long long li = it - J.first;
+    const int lt = (int)(li / nblk), blk = (int)(li % nblk);
+    const int ell0 = lt * G;
+    const int ell = ell0 + g;
+    const int ellc = ell < L ? ell : L - 1;
+    if (lt != cur_lt || j != cur_j) {
+      cur_lt = lt;
+      cur_j = j;
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const int i = t + T * r;
+        pr[r] = i < M ? J.pre[(size_t)ellc * M + i] : make_float2(0.f, 0.f);
+        ks[r] = J.kspec[(size_t)ellc * P + i];
+        po[r] = i < B ? J.post[(size_t)ellc * B + i] : make_float2(0.f, 0.f);
+      }
+    }
+    const float2* row = J.yhat + ((size_t)blk * L + ellc) * M;
+    float2 v[1][E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int i = t + T * r;
+      v[0][r] = i < M ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
+    }
+    block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], ks[r]);
+    block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int b = t + T * r;
+      if (b < B) tile[b * G + g] = cmul(v[0][r], po[r]);
+    }
+    __syncthreads();
+    float2* out = J.w + (size_t)blk * B * L + ell0;
+    for (int idx = threadIdx.x; idx < B * G; idx += blockDim.x) {
+      const int b = idx / G, gg = idx % G;
+      if (ell0 + gg < L) out[(size_t)b * L + gg] = tile[idx];
+    }
+    __syncthreads();
+  }
+}
+
+template <int P, int E, int G>
+static int run_space(const job_list<space_job>& jl, int max_B, const float2* tw, cudaStream_t s) {
+  constexpr int T = P / E;
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * G);
+  if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
+  FBST_TRY(allow_max_smem(k_czt_space_ula<P, E, G>));
+  const int grid = grid_for_items(jl.total, resident_ctas(k_czt_space_ula<P, E, G>, G * T, smem));
+  k_czt_space_ula<P, E, G><<<grid, G * T, smem, s>>>(jl, tw);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+// Compiled shapes (P, E, G); the first entry of each P is its default.
+#define FBST_SPACE_SHAPES(X)                                                                         \
+  X(16, 8, 16) X(32, 8, 16) X(64, 8, 16) X(64, 8, 8) X(128, 8, 8) X(128, 8, 4) X(128, 16, 8)           \
+  X(256, 8, 8) X(256, 8, 4) X(256, 8, 2) X(256, 16, 8) X(256, 16, 4) X(512, 8, 4) X(512, 8, 2)         \
+  X(512, 8, 8) X(512, 16, 4) X(512, 16, 8) X(512, 16, 2) X(1024, 8, 4) X(1024, 8, 2) X(1024, 16, 4)    \
+  X(1024, 16, 8) X(1024, 16, 2) X(2048, 16, 4) X(2048, 16, 2) X(2048, 8, 2) X(4096, 16, 2)
+
+int launch_space_jobs(const job_list<space_job>& jl, int P, fft_shape sh, int max_B, const float2* tw,
+                      cudaStream_t s) {
+  if (jl.total <= 0) return FBST_OK;
+#define FBST_X(p, e, g) \
+  if (P == p && sh.E == e && sh.G == g) return run_space<p, e, g>(jl, max_B, tw, s);
+  FBST_SPACE_SHAPES(FBST_X)
+#undef FBST_X
+  return FBST_ERR_UNSUPPORTED;
+}
+
+int space_shapes(int P, fft_shape* out, int cap) {
+  int n = 0;
+#define FBST_X(p, e, g) \
+  if (P == p && n < cap) out[n++] = fft_shape{e, g};
+  FBST_SPACE_SHAPES(FBST_X)
+#undef FBST_X
+  return n;
+}
+
+fft_shape space_shape(const fbst_plan_s* p) {
+  if (p->shape_space.E) return p->shape_space;
+  fft_shape d{0, 0};
+  space_shapes(p->info.P_space_x, &d, 1);
+  return d;
+}
+
+long long space_items(const space_job& j, fft_shape sh, int) {
+  return (long long)((j.L + sh.G - 1) / sh.G) * j.nblk;
+}
+
+space_job make_space_job(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk) {
+  const fbst_axis_tables& ax = p->ax[0];
+  return space_job{yhat, w, ax.pre, ax.kspec, ax.post, ax.Ma, ax.Ba, p->info.L, nblk, 0};
+}
+
+// ---------------------------------------------------------------------------------------------
+// Rectangular array (App. B): for each frequency, a chirp-z along y (my -> by) for every row kx,
+// then along x (mx -> bx) for every beam column c, both in shared memory. Work item = (tile of
+// TL consecutive frequencies, block). Both axes use size-P transforms.
+// ---------------------------------------------------------------------------------------------
+template <int P> struct ura_e { static constexpr int value = P >= 2048 ? 16 : (P >= 8 ? 8 : 2); };
+
+template <int P, int TL, int NTH>
+__global__ void __launch_bounds__(NTH)
+k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_axis_tables axx,
+                fbst_axis_tables axy, const float2* __restrict__ tw, int L, int nblk) {
+  constexpr int E = ura_e<P>::value;
+  constexpr int T = P / E;
+  constexpr int G = NTH / T;  // concurrent transforms
+  constexpr int SB = fft_smem_elems<float2>(P);
+  extern __shared__ float2 sm[];
+  const int mx = axx.Ma, bx = axx.Ba, my = axy.Ma, by = axy.Ba;
+  const int M = mx * my, B = bx * by;
+  const int g = threadIdx.x / T, t = threadIdx.x % T;
+  float2* fbuf = sm + g * SB;
+  float2* Z = sm + G * SB;      // [mx][by]
+  float2* tile = Z + mx * by;   // [B][TL]
+  const int ntile = (L + TL - 1) / TL;
+  long long it0, it1;
+  my_range((long long)ntile * nblk, &it0, &it1);
+  for (long long it = it0; it < it1; ++it) {
+    const int lt = (int)(it / nblk), blk = (int)(it % nblk);
+    const int ell0 = lt * TL;
+    for (int j = 0; j < TL; ++j) {
+      const int ell = min(ell0 + j, L - 1);
+      const float2* src = yhat + ((size_t)blk * L + ell) * M;
+      for (int kx0 = 0; kx0 < mx; kx0 += G) {
+        const int kx = kx0 + g;
+        const bool act = kx < mx;
+        float2 v[1][E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int ky = t + T * r;
+          v[0][r] = (act && ky < my) ? cmul(src[kx * my + ky], axy.pre[(size_t)ell * my + ky]) : make_float2(0.f, 0.f);
+        }
+        block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], axy.kspec[(size_t)ell * P + t + T * r]);
+        block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int c = t + T * r;
+          if (act && c < by) Z[kx * by + c] = cmul(v[0][r], axy.post[(size_t)ell * by + c]);
+        }
+      }
+      __syncthreads();
+      for (int c0 = 0; c0 < by; c0 += G) {
+        const int c = c0 + g;
+        const bool act = c < by;
+        float2 v[1][E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int kx = t + T * r;
+          v[0][r] = (act && kx < mx) ? cmul(Z[kx * by + c], axx.pre[(size_t)ell * mx + kx]) : make_float2(0.f, 0.f);
+        }
+        block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], axx.kspec[(size_t)ell * P + t + T * r]);
+        block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int a = t + T * r;
+          if (act && a < bx) tile[(a * by + c) * TL + j] = cmul(v[0][r], axx.post[(size_t)ell * bx + a]);
+        }
+      }
+      __syncthreads();
+    }
+    float2* out = w + (size_t)blk * B * L + ell0;
+    for (int idx = threadIdx.x; idx < B * TL; idx += blockDim.x) {
+      const int b = idx / TL, jj = idx % TL;
+      if (ell0 + jj < L) out[(size_t)b * L + jj] = tile[idx];
+    }
+    __syncthreads();
+  }
+}
+
+template <int P>
+static int czt_space_ura_P(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  constexpr int E = ura_e<P>::value;
+  constexpr int T = P / E;
+  constexpr int NTH = T >= 256 ? T : 256;
+  constexpr int G = NTH / T;
+  constexpr int TL = 4;
+  const fbst_info& in = p->info;
+  const fbst_axis_tables& axx = p->ax[0];
+  const fbst_axis_tables& axy = p->same_axes ? p->ax[0] : p->ax[1];
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)axx.Ma * axy.Ba +
+                                        (size_t)in.B * TL);
+  if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
+  FBST_TRY(allow_max_smem(k_czt_space_ura<P, TL, NTH>));
+  const long long items = (long long)((in.L + TL - 1) / TL) * nblk;
+  const int grid = grid_for_items(items, resident_ctas(k_czt_space_ura<P, TL, NTH>, NTH, smem));
+  k_czt_space_ura<P, TL, NTH><<<grid, NTH, smem, s>>>(yhat, w, axx, axy, p->tw32, in.L, nblk);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  if (nblk <= 0) return FBST_OK;
+  if (p->geom.kind == FBST_ULA) {
+    job_list<space_job> jl;
+    jl.n = 1;
+    jl.job[0] = make_space_job(p, yhat, w, nblk);
+    const fft_shape sh = space_shape(p);
+    jl.total = space_items(jl.job[0], sh, p->info.P_space_x);
+    return launch_space_jobs(jl, p->info.P_space_x, sh, p->ax[0].Ba, p->tw32, s);
+  }
+  if (p->info.P_space_x != p->info.P_space_y) return FBST_ERR_UNSUPPORTED;
+  switch (p->info.P_space_x) {
+    case 16: return czt_space_ura_P<16>(p, yhat, w, nblk, s);
+    case 32: return czt_space_ura_P<32>(p, yhat, w, nblk, s);
+    case 64: return czt_space_ura_P<64>(p, yhat, w, nblk, s);
+    case 128: return czt_space_ura_P<128>(p, yhat, w, nblk, s);
+    case 256: return czt_space_ura_P<256>(p, yhat, w, nblk, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace fbst

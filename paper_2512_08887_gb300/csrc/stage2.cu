@@ -1,10 +1,12 @@
 // Stage 2 of the FBST (Sec. V): beta_b = A_b^{-1} w_b, bhat_b = F_u beta_b.
 //
-// k_stage2_gs fuses, per (beam, block): the Gohberg-Semencul product (gs.cuh, six transforms of
-// size P_gs >= 2L-1) and the reconstruction chirp-z of F_u (Eq. (7)) evaluated by Bluestein
-// with S_rec input splits (S_rec forward transforms of size P_rec summed in frequency, one inverse).
-// One CTA owns one beam and a run of blocks; the beam's spectra stay in registers across blocks,
-// beta never leaves shared memory, and the only HBM traffic is w in and bhat out.
+// k_stage2_gs fuses, per (beam, block) work item: the Gohberg-Semencul product (gs.cuh, six
+// transforms of size P_gs >= 2L-1), optionally one FP32 refinement step (beta += GS(w - A_b beta),
+// the Toeplitz product through its circulant embedding), and the reconstruction chirp-z of F_u
+// (Eq. (7)) by Bluestein with S_rec input splits (S_rec forward transforms of size P_rec summed in
+// frequency, one inverse). beta never leaves shared memory; the only HBM traffic is w in and bhat
+// out. Work items of all jobs of a launch are flattened beam-major and split evenly over the
+// resident CTAs; a CTA keeps the current beam's spectra in registers.
 //
 // k_dense_fp32 applies the precomputed G_b = F_u A_b^{-1} (N x L, Sec. III-B) as a batched
 // complex GEMM over blocks on the FP32 CUDA cores.
@@ -13,6 +15,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "gs.cuh"
+#include "launch_util.cuh"
 
 namespace fbst {
 
@@ -20,10 +23,7 @@ template <int P> struct gs_e { static constexpr int value = P >= 4096 ? 16 : (P 
 
 template <int PG, int PR, int SR, bool IR>
 __global__ void __launch_bounds__(PG / gs_e<PG>::value)
-k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float2* __restrict__ XV,
-            const float2* __restrict__ Aspec,
-            const float2* __restrict__ pre_r, const float2* __restrict__ qspec, const float2* __restrict__ post_r,
-            const float2* __restrict__ tw, int B, int L, int N, int nblk, int blk_per_cta) {
+k_stage2_gs(const __grid_constant__ job_list<gs_job> jl, const float2* __restrict__ tw) {
   constexpr int EG = gs_e<PG>::value;
   constexpr int T = PG / EG;
   constexpr int ER = PR / T;
@@ -32,26 +32,29 @@ k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float
   extern __shared__ float2 sm[];
   float2* beta_s = sm + 2 * SBG;  // [L]
   const int t = threadIdx.x;
-  const int Lr = L / SR;
-  // Work item = (beam, block), beam-major; CTA c owns the contiguous range [c*I/G, (c+1)*I/G) of
-  // the I = B*nblk items and keeps the current beam's spectra in registers.
-  const long long items = (long long)B * nblk;
-  const long long it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
-  int b = -1;
+  long long it0, it1;
+  my_range(jl.total, &it0, &it1);
+  int j = 0, cur_j = -1, b_cur = -1;
   float2 X[EG], Vv[EG];
 
   for (long long it = it0; it < it1; ++it) {
-    const int blk = (int)(it % nblk);
-    if ((int)(it / nblk) != b) {
-      b = (int)(it / nblk);
-      const float2* xv = XV + (size_t)b * 2 * PG;
+    while (j + 1 < jl.n && jl.job[j + 1].first <= it) ++j;
+    const gs_job& J = jl.job[j];
+    const int B = J.B, L = J.L, N = J.N, nblk = J.nblk;
+    const int Lr = L / SR;
+    const long long li = it - J.first;
+    const int b = (int)(li / nblk), blk = (int)(li % nblk);
+    if (b != b_cur || j != cur_j) {
+      b_cur = b;
+      cur_j = j;
+      const float2* xv = J.XV + (size_t)b * 2 * PG;
 #pragma unroll
       for (int r = 0; r < EG; ++r) {
         X[r] = xv[t + T * r];
         Vv[r] = xv[PG + t + T * r];
       }
     }
-    const float2* wb = w + ((size_t)blk * B + b) * L;
+    const float2* wb = J.w + ((size_t)blk * B + b) * L;
     float2 v[EG];
 #pragma unroll
     for (int r = 0; r < EG; ++r) {
@@ -63,7 +66,7 @@ k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float
       // One refinement step: r = w - A beta (Toeplitz product through its circulant embedding),
       // beta += GS(r). The residual's rounding error lies mostly where A_b is small, which F_u
       // (whose rows are rows of F_b) does not see; the GS cancellation error is removed.
-      const float2* As = Aspec + (size_t)b * PG;
+      const float2* As = J.Aspec + (size_t)b * PG;
       float2 a[1][EG];
 #pragma unroll
       for (int r = 0; r < EG; ++r) a[0][r] = (t + T * r < L) ? v[r] : make_float2(0.f, 0.f);
@@ -94,80 +97,86 @@ k_stage2_gs(const float2* __restrict__ w, float2* __restrict__ bhat, const float
 #pragma unroll
       for (int r = 0; r < ER; ++r) {
         const int i = t + T * r;
-        x[h][r] = i < Lr ? cmul(beta_s[h * Lr + i], pre_r[h * Lr + i]) : make_float2(0.f, 0.f);
+        x[h][r] = i < Lr ? cmul(beta_s[h * Lr + i], J.pre_r[h * Lr + i]) : make_float2(0.f, 0.f);
       }
     }
     block_fft<PR, ER, SR, -1>(x, sm, tw, t);
     float2 R[1][ER];
 #pragma unroll
     for (int r = 0; r < ER; ++r) {
-      float2 acc = cmul(x[0][r], qspec[t + T * r]);
+      float2 acc = cmul(x[0][r], J.qspec[t + T * r]);
 #pragma unroll
-      for (int h = 1; h < SR; ++h) acc = cadd(acc, cmul(x[h][r], qspec[h * PR + t + T * r]));
+      for (int h = 1; h < SR; ++h) acc = cadd(acc, cmul(x[h][r], J.qspec[h * PR + t + T * r]));
       R[0][r] = acc;
     }
     block_fft<PR, ER, 1, +1>(R, sm, tw, t);
-    float2* ob = bhat + ((size_t)blk * B + b) * N;
+    float2* ob = J.bhat + ((size_t)blk * B + b) * N;
 #pragma unroll
     for (int r = 0; r < ER; ++r) {
       const int n = t + T * r;
-      if (n < N) ob[n] = cmul(R[0][r], post_r[n]);
+      if (n < N) ob[n] = cmul(R[0][r], J.post_r[n]);
     }
   }
 }
 
 template <int PG, int PR, int SR, bool IR>
-static int stage2_gs_P(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
-  constexpr int EG = gs_e<PG>::value;
-  constexpr int T = PG / EG;
-  const fbst_info& in = p->info;
-  const size_t smem = sizeof(float2) * (2 * (size_t)fft_smem_elems<float2>(PG) + in.L);
-  FBST_CUDA_TRY(cudaFuncSetAttribute(k_stage2_gs<PG, PR, SR, IR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
-  FBST_CUDA_TRY(cudaGetDevice(&dev));
-  FBST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  FBST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage2_gs<PG, PR, SR, IR>, T, smem));
-  const long long items = (long long)in.B * nblk;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(items, (long long)sms * std::max(1, per_sm)));
-  k_stage2_gs<PG, PR, SR, IR><<<grid, T, smem, s>>>(w, bhat, p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, p->tw32,
-                                                in.B, in.L, in.N, nblk, 0);
+static int run_gs(const job_list<gs_job>& jl, int max_L, const float2* tw, cudaStream_t s) {
+  constexpr int T = PG / gs_e<PG>::value;
+  const size_t smem = sizeof(float2) * (2 * (size_t)fft_smem_elems<float2>(PG) + max_L);
+  if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
+  FBST_TRY(allow_max_smem(k_stage2_gs<PG, PR, SR, IR>));
+  const int grid = grid_for_items(jl.total, resident_ctas(k_stage2_gs<PG, PR, SR, IR>, T, smem));
+  k_stage2_gs<PG, PR, SR, IR><<<grid, T, smem, s>>>(jl, tw);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
 template <int PG, bool IR>
-static int stage2_gs_PGI(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
-  const int PR = p->info.P_rec, SR = p->info.S_rec;
+static int gs_PGI(const job_list<gs_job>& jl, int PR, int SR, int max_L, const float2* tw, cudaStream_t s) {
   if constexpr (gs_e<PG>::value >= 4) {
-    if (2 * PR == PG && SR == 2) return stage2_gs_P<PG, PG / 2, 2, IR>(p, w, bhat, nblk, s);
-    if (2 * PR == PG && SR == 1) return stage2_gs_P<PG, PG / 2, 1, IR>(p, w, bhat, nblk, s);
+    if (2 * PR == PG && SR == 2) return run_gs<PG, PG / 2, 2, IR>(jl, max_L, tw, s);
+    if (2 * PR == PG && SR == 1) return run_gs<PG, PG / 2, 1, IR>(jl, max_L, tw, s);
   }
-  if (PR == PG && SR == 1) return stage2_gs_P<PG, PG, 1, IR>(p, w, bhat, nblk, s);
-  if (PR == PG && SR == 2) return stage2_gs_P<PG, PG, 2, IR>(p, w, bhat, nblk, s);
+  if (PR == PG && SR == 1) return run_gs<PG, PG, 1, IR>(jl, max_L, tw, s);
+  if (PR == PG && SR == 2) return run_gs<PG, PG, 2, IR>(jl, max_L, tw, s);
   return FBST_ERR_UNSUPPORTED;
 }
 
 template <int PG>
-static int stage2_gs_PG(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
-  return p->info.stage2 == FBST_STAGE2_GS_IR1 ? stage2_gs_PGI<PG, true>(p, w, bhat, nblk, s)
-                                              : stage2_gs_PGI<PG, false>(p, w, bhat, nblk, s);
+static int gs_PG(const job_list<gs_job>& jl, int PR, int SR, bool IR, int max_L, const float2* tw, cudaStream_t s) {
+  return IR ? gs_PGI<PG, true>(jl, PR, SR, max_L, tw, s) : gs_PGI<PG, false>(jl, PR, SR, max_L, tw, s);
+}
+
+int launch_gs_jobs(const job_list<gs_job>& jl, int PG, int PR, int SR, bool IR, int max_L, const float2* tw,
+                   cudaStream_t s) {
+  if (jl.total <= 0) return FBST_OK;
+  switch (PG) {
+    case 16: return gs_PG<16>(jl, PR, SR, IR, max_L, tw, s);
+    case 32: return gs_PG<32>(jl, PR, SR, IR, max_L, tw, s);
+    case 64: return gs_PG<64>(jl, PR, SR, IR, max_L, tw, s);
+    case 128: return gs_PG<128>(jl, PR, SR, IR, max_L, tw, s);
+    case 256: return gs_PG<256>(jl, PR, SR, IR, max_L, tw, s);
+    case 512: return gs_PG<512>(jl, PR, SR, IR, max_L, tw, s);
+    case 1024: return gs_PG<1024>(jl, PR, SR, IR, max_L, tw, s);
+    case 2048: return gs_PG<2048>(jl, PR, SR, IR, max_L, tw, s);
+    case 4096: return gs_PG<4096>(jl, PR, SR, IR, max_L, tw, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+gs_job make_gs_job(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk) {
+  const fbst_info& in = p->info;
+  return gs_job{w, bhat, p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, in.B, in.L, in.N, nblk, 0};
 }
 
 int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
-  if (nblk > 65535) return FBST_ERR_UNSUPPORTED;
-  switch (p->info.P_gs) {
-    case 16: return stage2_gs_PG<16>(p, w, bhat, nblk, s);
-    case 32: return stage2_gs_PG<32>(p, w, bhat, nblk, s);
-    case 64: return stage2_gs_PG<64>(p, w, bhat, nblk, s);
-    case 128: return stage2_gs_PG<128>(p, w, bhat, nblk, s);
-    case 256: return stage2_gs_PG<256>(p, w, bhat, nblk, s);
-    case 512: return stage2_gs_PG<512>(p, w, bhat, nblk, s);
-    case 1024: return stage2_gs_PG<1024>(p, w, bhat, nblk, s);
-    case 2048: return stage2_gs_PG<2048>(p, w, bhat, nblk, s);
-    case 4096: return stage2_gs_PG<4096>(p, w, bhat, nblk, s);
-    default: return FBST_ERR_UNSUPPORTED;
-  }
+  const fbst_info& in = p->info;
+  job_list<gs_job> jl;
+  jl.n = 1;
+  jl.job[0] = make_gs_job(p, w, bhat, nblk);
+  jl.total = (long long)in.B * nblk;
+  return launch_gs_jobs(jl, in.P_gs, in.P_rec, in.S_rec, in.stage2 == FBST_STAGE2_GS_IR1, in.L, p->tw32, s);
 }
 
 // ---------------------------------------------------------------------------------------------
