@@ -246,6 +246,59 @@ def run_c4(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_c5(args) -> None:
+    """C5: Poisson request streams at rates 1e2..1e5 /s over the 64 C4 arrays (one block per
+    request, two seeded data blocks per array), served by the continuous-batching server and by the
+    plain one-request-at-a-time server on the same GPU; p50/p99 latency and throughput per rate."""
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300 import autotune, serve
+    from paper_2512_08887_gb300.build import build
+    from synth import configs
+    build()
+    torch.cuda.set_device(0)
+    insts = configs.c4_instances(count=64)
+    plans = [fb.Plan(fb.make_geometry("ula", d["M"]), d["N"], fb.make_band(d["frac_bw"], max_blocks=32))
+             for d in insts]
+    if not args.no_tune:
+        for p in plans:
+            autotune.tune(p, 1)
+    rng = np.random.default_rng(55)
+    pools = []
+    for d in insts:
+        blocks = [torch.from_numpy(d["y"]).pin_memory()]
+        noise = 0.1 * (rng.standard_normal(d["y"].shape) + 1j * rng.standard_normal(d["y"].shape))
+        blocks.append(torch.from_numpy((d["y"] + noise).astype(np.complex64)).pin_memory())
+        pools.append(blocks)
+    req_bytes = [8 * (p.M * p.N + p.B * p.N) for p in plans]
+    req_work = [p.B * p.N for p in plans]
+    sched = lambda: serve.Scheduler(req_bytes, args.mem_budget, 32, req_work, args.batch_work)
+    rates = [float(r) for r in args.rates.split(",")]
+    # Warm both paths (allocator, one-time kernel set-up).
+    warm = serve.poisson_requests(1e5, 128, pools, seed=1)
+    ex = serve.GPUExecutor(plans, n_streams=args.streams)
+    serve.run_loop(warm, sched(), ex)
+    serve.serve_plain(serve.poisson_requests(1e5, 64, pools, seed=2), plans)
+    results = []
+    for k, rate in enumerate(rates):
+        reqs = serve.poisson_requests(rate, args.requests, pools, seed=100 + k)
+        st_b = serve.run_loop(reqs, sched(), ex)
+        reqs_p = serve.poisson_requests(rate, args.requests, pools, seed=100 + k)
+        st_p = serve.serve_plain(reqs_p, plans)
+        results.append({"rate_per_s": rate, "batched": st_b, "plain": st_p})
+        print(json.dumps({"rate": rate, "batched": st_b, "plain": st_p}), file=sys.stderr, flush=True)
+    ex.close()
+    top = results[-1]
+    line = {"metric": METRIC, "value": top["batched"]["beam_samples_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.requests, "warmup": 128, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"C5: Poisson requests over the 64 C4 arrays, {args.requests} per rate, "
+                                   f"{args.streams} streams, memory budget {args.mem_budget >> 20} MiB"},
+            "latency_ms": {"p50": top["batched"]["p50_ms"], "p99": top["batched"]["p99_ms"]},
+            "per_rate": results}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -290,6 +343,11 @@ def main() -> None:
     ap.add_argument("--stage2", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--rates", default="1e2,3e2,1e3,3e3,1e4,3e4,1e5")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--streams", type=int, default=3)
+    ap.add_argument("--mem-budget", type=int, default=8 << 30)
+    ap.add_argument("--batch-work", type=float, default=4e6)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -298,6 +356,9 @@ def main() -> None:
         return
     if args.workload == "C4":
         run_c4(args)
+        return
+    if args.workload == "C5":
+        run_c5(args)
         return
 
     import torch

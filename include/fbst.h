@@ -203,6 +203,10 @@ int fbst_batch_create(fbst_batch_t* out, const fbst_plan_t* plans, int count);
  * graph; later runs with the same arguments replay the graph. Results equal per-plan fbst_execute. */
 int fbst_batch_execute(fbst_batch_t b, const void* const* y, void* const* bhat, const int* nblk, void* stream);
 
+/* Same grouped launches as fbst_batch_execute, enqueued directly without capturing a graph (for
+ * callers whose pointer sets change on every call, such as a continuous-batching server). */
+int fbst_batch_enqueue(fbst_batch_t b, const void* const* y, void* const* bhat, const int* nblk, void* stream);
+
 /* Kernels in one graph replay of the batch (0 before the first run). */
 int fbst_batch_launch_count(fbst_batch_t b);
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "fbst_launch_count": (_I, [_VP, _I]),
     "fbst_batch_create": (_I, [C.POINTER(_VP), C.POINTER(_VP), _I]),
     "fbst_batch_execute": (_I, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_I), _VP]),
+    "fbst_batch_enqueue": (_I, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_I), _VP]),
     "fbst_batch_launch_count": (_I, [_VP]),
     "fbst_batch_destroy": (_I, [_VP]),
     "fbst_autotune": (_I, [_VP, _I, _VP, C.POINTER(_I)]),
@@ -264,6 +265,14 @@ class Batch:
         ba = (C.c_void_p * n)(*[_ptr(v) for v in bhats])
         na = (C.c_int * n)(*[int(v) for v in nblks])
         _check(self._lib.fbst_batch_execute(self._h, ya, ba, na, _stream(stream)), "fbst_batch_execute")
+
+    def enqueue(self, ys, bhats, nblks, stream=None) -> None:
+        """Grouped launches without graph capture (pointer sets that change every call)."""
+        n = len(self.plans)
+        ya = (C.c_void_p * n)(*[_ptr(v) for v in ys])
+        ba = (C.c_void_p * n)(*[_ptr(v) for v in bhats])
+        na = (C.c_int * n)(*[int(v) for v in nblks])
+        _check(self._lib.fbst_batch_enqueue(self._h, ya, ba, na, _stream(stream)), "fbst_batch_enqueue")
 
     def launch_count(self) -> int:
         return int(self._lib.fbst_batch_launch_count(self._h))

@@ -223,6 +223,19 @@ int fbst_batch_execute(fbst_batch_t bt, const void* const* y, void* const* bhat,
   return FBST_OK;
 }
 
+int fbst_batch_enqueue(fbst_batch_t bt, const void* const* y, void* const* bhat, const int* nblk, void* stream) {
+  if (!bt || !y || !bhat || !nblk) return FBST_ERR_INVALID;
+  const int n = (int)bt->plans.size();
+  for (int i = 0; i < n; ++i) {
+    if (nblk[i] < 0 || nblk[i] > bt->plans[i]->band.max_blocks) return FBST_ERR_INVALID;
+    if (nblk[i] > 0 && (!y[i] || !bhat[i] || (reinterpret_cast<uintptr_t>(y[i]) & 15u) ||
+                        (reinterpret_cast<uintptr_t>(bhat[i]) & 15u)))
+      return FBST_ERR_INVALID;
+  }
+  int launches = 0;
+  return enqueue_batch(bt, y, bhat, nblk, reinterpret_cast<cudaStream_t>(stream), &launches);
+}
+
 int fbst_batch_launch_count(fbst_batch_t bt) { return bt ? bt->launches : 0; }
 
 int fbst_batch_destroy(fbst_batch_t bt) {
