@@ -1,10 +1,14 @@
 """Benchmark of the FBST hot path on GB300.
 
 Default workload (C2): 256-element linear array, fb = 0.5, N = 256 snapshots per block, B = 256
-beams, L = 512, 64 contiguous blocks of one record per step, complex64 in and out, FP32 maths,
-Gohberg-Semencul stage 2. One step = fbst_execute over the 64 blocks (all three kernels).
+beams, L = 512, 64 contiguous blocks of one record per step, complex64 in and out. Stage 1 (the
+fan chirp-z) in FP32 on the CUDA cores; stage 2 by default the precomputed-inverse apply on the
+tensor cores in split TF32 with split FP32 accumulation (FP32-class: measured rel err ~3e-6 vs the
+FP64 oracle, reported on every run); --stage2 gs_ir1 selects the Gohberg-Semencul path, dense_fp32
+the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 gs|dense_fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
+                  [--workload C2|C3|ULA1024|C4|C5]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own 64 blocks (weak
 scaling; the method has no cross-block exchange, so there is no collective on the data path).
@@ -143,6 +147,10 @@ def workload(args):
         nb = args.nblk or configs.CONFIGS["C2"]["nblk"]
         return dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, nblk=nb, name="C2"), \
             lambda: configs.config_data("C2", nblk=nb)["y"]
+    if args.workload == "C3":
+        nb = args.nblk or configs.CONFIGS["C3"]["nblk"]
+        return dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, nblk=nb, name="C3"), \
+            lambda: configs.config_data("C3", nblk=nb, Q=64)["y"]
     if args.workload == "ULA1024":
         # Large linear array (the paper's scaling regime): M = B = 1024, N = 512, fb = 0.5.
         def gen():
@@ -340,7 +348,7 @@ def main() -> None:
     ap.add_argument("--impl", default="fbst", choices=["fbst", "reference"])
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--nblk", type=int, default=None)
-    ap.add_argument("--stage2", default="auto")
+    ap.add_argument("--stage2", default="dense_tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--rates", default="1e2,3e2,1e3,3e3,1e4,3e4,1e5")
@@ -364,6 +372,7 @@ def main() -> None:
     import torch
     import paper_2512_08887_gb300 as fb
     from paper_2512_08887_gb300.build import build
+    from paper_2512_08887_gb300.dist import max_over_ranks, whole_job_rate
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -430,13 +439,9 @@ def main() -> None:
     wall = time.perf_counter() - wall0
     clocks = sampler.stop() if sampler else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms))
     units = float(nblk) * B * N * world
-    value = units * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(float(nblk) * B * N * args.steps, world, total_ms / 1e3)
 
     # Per-kernel live timing: each kernel through its own C-ABI stage call, events on its stream.
     kin = min(args.steps, 200)
@@ -468,11 +473,7 @@ def main() -> None:
         t0 = time.perf_counter()
         plan.execute_host(y_host, out_host, nblk)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_t))
 
     if rank != 0:
         if dist is not None:
@@ -508,8 +509,10 @@ def main() -> None:
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{w['name']}: ULA M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if info.stage2 <= 3 else f"f32 stage 1 + {fb.STAGE2_NAMES[info.stage2][6:]} tensor-core stage 2",
+        "data": "synthetic",
+        "config": {"workload": f"{w['name']}: {w['kind'].upper()} M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
                                f"{nblk} blocks/step per GPU, complex64",
                    "M": M, "B": B, "N": N, "L": info.L, "nblk_per_gpu": nblk, "stage2": fb.STAGE2_NAMES[info.stage2],
                    "l2": "flushed before every timed step (256 MiB write, untimed)",

@@ -248,7 +248,12 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM, b = blockIdx.y, blk0 = blockIdx.z * NB;
   const int nchunks = (L + KELEM - 1) / KELEM;
-  constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : (2 * NB <= 64 ? 64 : (2 * NB <= 128 ? 128 : 256));
+  // KACC partial accumulators (K-chunk c goes to accumulator c % KACC), summed in FP32 in the
+  // epilogue: the tensor pipe's accumulation error grows with the number of terms it sums, so
+  // shorter partial sums keep the split-precision variants near FP32 accuracy.
+  constexpr int KACC = 2 * NB * 4 <= 512 ? 4 : (2 * NB * 2 <= 512 ? 2 : 1);
+  constexpr uint32_t COLS = 2 * NB * KACC;
+  constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -299,7 +304,6 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     // ---------------- MMA issuer ----------------
     constexpr uint32_t ID_POS = make_idesc(TR::FMT, kTileM, NB, false);
     constexpr uint32_t ID_NEG = make_idesc(TR::FMT, kTileM, NB, true);
-    const uint32_t d_re = tmem, d_im = tmem + NB;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int s = c % STAGES;
@@ -311,6 +315,7 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(smem + s * SM::STAGE_BYTES);
+      const uint32_t d_re = tmem + (uint32_t)((c % KACC) * 2 * NB), d_im = d_re + NB;
       // Planes: TERMS == 1 -> {re, im}; TERMS == 3 -> {re_hi, re_lo, im_hi, im_lo}.
       constexpr int RE_HI = 0, RE_LO = (TR::TERMS == 3 ? 1 : 0), IM_HI = (TR::TERMS == 3 ? 2 : 1),
                     IM_LO = (TR::TERMS == 3 ? 3 : 1);
@@ -318,7 +323,7 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       for (int k = 0; k < KSTEPS; ++k) {
         auto da = [&](int pl) { return smem_desc_sw128(st + pl * SM::A_TILE + k * 32); };
         auto db = [&](int pl) { return smem_desc_sw128(st + NPL * SM::A_TILE + pl * SM::B_TILE + k * 32); };
-        const uint32_t acc0 = (c > 0 || k > 0) ? 1u : 0u;
+        const uint32_t acc0 = (c >= KACC || k > 0) ? 1u : 0u;
         // C_re = G_re W_re - G_im W_im ; C_im = G_re W_im + G_im W_re
         mma_issue<V>(d_re, da(RE_HI), db(RE_HI), ID_POS, acc0);
         mma_issue<V>(d_re, da(IM_HI), db(IM_HI), ID_NEG, 1u);
@@ -350,10 +355,21 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     const int n = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
+    const int nacc = nchunks < KACC ? nchunks : KACC;
     for (int j0 = 0; j0 < NB; j0 += 16) {
       float re[16], im[16];
       tmem_ld16(lane_base + j0, re);
       tmem_ld16(lane_base + NB + j0, im);
+      for (int q = 1; q < nacc; ++q) {
+        float re2[16], im2[16];
+        tmem_ld16(lane_base + q * 2 * NB + j0, re2);
+        tmem_ld16(lane_base + q * 2 * NB + NB + j0, im2);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          re[jj] += re2[jj];
+          im[jj] += im2[jj];
+        }
+      }
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         const int blk = blk0 + j0 + jj;
