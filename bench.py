@@ -71,8 +71,9 @@ def flop_model(info) -> dict:
     return {"czt_time": time_per_sensor * M, "czt_space": space_per_freq * L, "stage2": stage2}
 
 
-# Tensor-core variants: (planes of G and W, bytes per element, products per complex term, peak dtype).
-TC_VARIANTS = {4: (4, 2, 3, "bf16"), 5: (2, 4, 1, "tf32"), 6: (4, 4, 3, "tf32")}
+# Tensor-core variants: (planes of G, bytes per element, products per complex term, peak dtype,
+# passes over w: prepared planes = read + write + read; the fused TF32x3 kernel reads w once).
+TC_VARIANTS = {4: (4, 2, 3, "bf16", 3), 5: (2, 4, 1, "tf32", 3), 6: (2, 4, 3, "tf32", 1)}
 
 
 def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str) -> dict:
@@ -82,14 +83,14 @@ def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: st
     flops = flop_model(info)[kernel] * nblk
     M, N, B, L = info.M, info.N, info.B, info.L
     if kernel == "stage2" and info.stage2 in TC_VARIANTS:
-        npl, esz, terms, dt = TC_VARIANTS[info.stage2]
-        nbytes = float(B) * npl * N * L * esz + 2.0 * B * L * nblk * 8 + B * N * nblk * 8.0
+        npl, esz, terms, dt, wpass = TC_VARIANTS[info.stage2]
+        nbytes = float(B) * npl * N * L * esz + wpass * B * L * nblk * 8.0 + B * N * nblk * 8.0
         hbm = float(peaks["hbm_gbs"])
         tc_peak = float(peaks["bf16_tflops"]) * (1.0 if dt == "bf16" else 0.5)  # nominal 2:1 bf16:tf32
         if nbytes / (hbm * 1e9) >= terms * flops / (tc_peak * 1e12):
             ach = nbytes / (ms / 1e3) / 1e9
             return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "peak_source": f"{peak_kind} hbm_gbs; bytes = G planes + W planes in/out + bhat"}
+                    "peak_source": f"{peak_kind} hbm_gbs; bytes = G planes + w passes + bhat"}
         ach = terms * flops / (ms / 1e3) / 1e12
         return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
                 "peak_source": f"{peak_kind} bf16_tflops x {'1' if dt == 'bf16' else '0.5 (tf32 nominal ratio)'}"}

@@ -11,11 +11,23 @@
 //            hi*hi + hi*lo + lo*hi: FP32-class accuracy
 // always with FP32 accumulation in tensor memory.
 //
-// Kernel structure (one CTA = one beam x 128 output samples x up to NB blocks, 128 threads):
+// Long sums in TF32 lose accuracy as K = L grows, so the K chunks are spread over KACC partial
+// accumulators in tensor memory (chunk c adds into accumulator c % KACC, up to 4 of them within
+// the 512 columns) and the epilogue adds the partials in FP32.
+//
+// BF16X3 and TF32 (k_dense_tc: one CTA = one beam x 128 output samples x up to NB blocks, 128
+// threads) read operands that separate kernels have already split into planes:
 //   thread 0  : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, one mbarrier per stage)
 //   thread 32 : MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = NB, K = 32 bytes per step)
-//   warp 1    : tensor-memory allocation / release (2 accumulators x NB columns)
+//   warp 1    : tensor-memory allocation / release (2 x NB columns per accumulator, KACC of them)
 //   warps 0-3 : epilogue (tcgen05.ld 32x32b, rows = samples, coalesced complex64 stores)
+// TF32X3 (k_dense_tc_fused, 256 threads) reads plain FP32 planes of G and the stage-1 output w as
+// it is (interleaved complex64) and splits both in shared memory, so no split pass goes through HBM:
+//   thread 0  : TMA producer (G planes with the 128-byte swizzle; raw w rows without swizzle)
+//   warp 1    : MMA issuer and tensor-memory owner
+//   warps 4-7 : converters: G and raw w -> TF32 hi / FP32 residual planes in the swizzled layout
+//               the MMA reads (cvt.rna.tf32), one mbarrier arrival per thread per stage
+//   warps 0-3 : epilogue as above
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel records FBST_ERR_TIMEOUT
 // in the plan's status word, waits (bounded) for its copies in flight, frees its tensor memory
 // and returns.
@@ -385,6 +397,235 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 }
 
 // ---------------------------------------------------------------------------------------------
+// Fused TF32x3 kernel: the plan keeps G_b as plain FP32 real/imaginary planes and the kernel reads
+// the interleaved complex64 w tiles straight from stage 1; a converter warpgroup splits both into
+// TF32 (hi, lo) planes in shared memory before the MMA thread consumes them. Compared with
+// pre-split operands this halves the bytes of G and removes the W preparation pass.
+//   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ warp 1 TMEM alloc/free)
+//   warps 4-7     : converters        warps 0-3     : epilogue
+// ---------------------------------------------------------------------------------------------
+template <int NB>
+struct fused_smem {
+  static constexpr int STAGES = 2;
+  static constexpr int A_TILE = kTileM * kRowBytes;    // one 128-row plane of 32 FP32 values per row
+  static constexpr int B_TILE = NB * kRowBytes;
+  static constexpr int WRAW_OFF = 4 * A_TILE;          // A planes: re_hi, im_hi (TMA, split in place), re_lo, im_lo
+  static constexpr int WPL_OFF = WRAW_OFF + 2 * B_TILE; // two raw interleaved w boxes (16 complex per row each)
+  static constexpr int STAGE_BYTES = WPL_OFF + 4 * B_TILE;  // W planes: re_hi, re_lo, im_hi, im_lo
+  static constexpr int TMA_BYTES = 2 * A_TILE + 2 * B_TILE;
+  static constexpr int BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ float4 rna4(float4 x) {
+  return make_float4(round_tf32(x.x), round_tf32(x.y), round_tf32(x.z), round_tf32(x.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+template <int NB>
+__global__ void __launch_bounds__(256, 1)
+k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
+                 float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
+  using SM = fused_smem<NB>;
+  constexpr int STAGES = SM::STAGES;
+  constexpr int KELEM = kRowBytes / 4;   // 32 FP32 values of K per chunk
+  constexpr int KSTEPS = kRowBytes / 32; // MMAs of K = 8 per chunk
+  constexpr int KACC = 2 * NB * 4 <= 512 ? 4 : (2 * NB * 2 <= 512 ? 2 : 1);
+  constexpr uint32_t COLS = 2 * NB * KACC;
+  constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * SM::STAGE_BYTES);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTileM, b = blockIdx.y, blk0 = blockIdx.z * NB;
+  const int nchunks = (L + KELEM - 1) / KELEM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES;
+      if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) {
+        atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * SM::STAGE_BYTES;
+      mbar_expect_tx(&full[s], SM::TMA_BYTES);
+      tma_load_3d(st, &mapA, &full[s], c * KELEM, m0, b * 2 + 0);
+      tma_load_3d(st + SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * 2 + 1);
+      tma_load_3d(st + SM::WRAW_OFF, &mapW, &full[s], 2 * c * KELEM, b, blk0);
+      tma_load_3d(st + SM::WRAW_OFF + SM::B_TILE, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
+      issued = c + 1;
+    }
+    if (*abort_flag) {
+      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+        (void)mbar_wait(&full[c % STAGES], (c / STAGES) & 1);
+    }
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t ID_POS = make_idesc(2u, kTileM, NB, false);
+    constexpr uint32_t ID_NEG = make_idesc(2u, kTileM, NB, true);
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES;
+      if (!mbar_wait(&conv[s], (c / STAGES) & 1)) {
+        atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * SM::STAGE_BYTES);
+      const uint32_t d_re = tmem + (uint32_t)((c % KACC) * 2 * NB), d_im = d_re + NB;
+      constexpr int ARH = 0, AIH = 1, ARL = 2, AIL = 3;  // A planes
+      constexpr int WRH = 0, WRL = 1, WIH = 2, WIL = 3;  // W planes
+#pragma unroll
+      for (int k = 0; k < KSTEPS; ++k) {
+        auto da = [&](int pl) { return smem_desc_sw128(st + pl * SM::A_TILE + k * 32); };
+        auto db = [&](int pl) { return smem_desc_sw128(st + SM::WPL_OFF + pl * SM::B_TILE + k * 32); };
+        const uint32_t acc0 = (c >= KACC || k > 0) ? 1u : 0u;
+        // C_re = G_re W_re - G_im W_im ; C_im = G_re W_im + G_im W_re ; each as hi*hi + hi*lo + lo*hi
+        mma_issue<TC_TF32X3>(d_re, da(ARH), db(WRH), ID_POS, acc0);
+        mma_issue<TC_TF32X3>(d_re, da(AIH), db(WIH), ID_NEG, 1u);
+        mma_issue<TC_TF32X3>(d_im, da(ARH), db(WIH), ID_POS, acc0);
+        mma_issue<TC_TF32X3>(d_im, da(AIH), db(WRH), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_re, da(ARH), db(WRL), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_re, da(ARL), db(WRH), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_re, da(AIH), db(WIL), ID_NEG, 1u);
+        mma_issue<TC_TF32X3>(d_re, da(AIL), db(WIH), ID_NEG, 1u);
+        mma_issue<TC_TF32X3>(d_im, da(ARH), db(WIL), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_im, da(ARL), db(WIH), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_im, da(AIH), db(WRL), ID_POS, 1u);
+        mma_issue<TC_TF32X3>(d_im, da(AIL), db(WRH), ID_POS, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 128;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES;
+      if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
+        atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      uint8_t* st = smem + s * SM::STAGE_BYTES;
+      // A: split each FP32 value into TF32 hi (in place) and the FP32 remainder (lo plane); the
+      // operation is elementwise, so the swizzled positions carry over unchanged.
+#pragma unroll 4
+      for (int i = ct; i < 2 * kTileM * 8; i += 128) {
+        const int pl = i / (kTileM * 8), off = (i % (kTileM * 8)) * 16;
+        float4* hp = reinterpret_cast<float4*>(st + pl * SM::A_TILE + off);
+        const float4 x = *hp;
+        const float4 hi = rna4(x);
+        *hp = hi;
+        *reinterpret_cast<float4*>(st + (2 + pl) * SM::A_TILE + off) = sub4(x, hi);
+      }
+      // W: deinterleave 4 complex values (two raw 16-byte chunks) into one 16-byte chunk of each of
+      // the four planes, at the 128-byte-swizzled position of (row r, chunk q).
+#pragma unroll 2
+      for (int j = ct; j < NB * 8; j += 128) {
+        const int r = j >> 3, q = j & 7;
+        const uint8_t* raw = st + SM::WRAW_OFF + (q >> 2) * SM::B_TILE + r * kRowBytes + (q & 3) * 32;
+        const float4 a = *reinterpret_cast<const float4*>(raw);
+        const float4 bb = *reinterpret_cast<const float4*>(raw + 16);
+        const float4 re = make_float4(a.x, a.z, bb.x, bb.z), im = make_float4(a.y, a.w, bb.y, bb.w);
+        const float4 rh = rna4(re), ih = rna4(im);
+        const int off = r * kRowBytes + ((q ^ (r & 7)) << 4);
+        uint8_t* wp = st + SM::WPL_OFF + off;
+        *reinterpret_cast<float4*>(wp + 0 * SM::B_TILE) = rh;
+        *reinterpret_cast<float4*>(wp + 1 * SM::B_TILE) = sub4(re, rh);
+        *reinterpret_cast<float4*>(wp + 2 * SM::B_TILE) = ih;
+        *reinterpret_cast<float4*>(wp + 3 * SM::B_TILE) = sub4(im, ih);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+    }
+  }
+  __syncwarp();
+
+  // ---------------- Epilogue: warps 0-3 ----------------
+  if (warp < 4) {
+    const bool have = mbar_wait(done, 0);
+    if (!have) {
+      if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
+    } else if (!*abort_flag) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int n = m0 + warp * 32 + lane;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const int nacc = nchunks < KACC ? nchunks : KACC;
+#pragma unroll 1
+      for (int j0 = 0; j0 < NB; j0 += 16) {
+        float re[16], im[16];
+        tmem_ld16(lane_base + j0, re);
+        tmem_ld16(lane_base + NB + j0, im);
+        for (int q = 1; q < nacc; ++q) {
+          float re2[16], im2[16];
+          tmem_ld16(lane_base + q * 2 * NB + j0, re2);
+          tmem_ld16(lane_base + q * 2 * NB + NB + j0, im2);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            re[jj] += re2[jj];
+            im[jj] += im2[jj];
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int blk = blk0 + j0 + jj;
+          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj], im[jj]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// G [B][N][L] complex64 -> FP32 planes [B][2][N][L] (real, imaginary).
+__global__ void k_tc_planes_f32(const float2* __restrict__ G, float* __restrict__ out, int B, int N, int L) {
+  const size_t per_beam = (size_t)N * L;
+  const size_t total = (size_t)B * per_beam;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / per_beam, r = i % per_beam;
+    const float2 g = G[i];
+    out[(b * 2 + 0) * per_beam + r] = g.x;
+    out[(b * 2 + 1) * per_beam + r] = g.y;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -416,6 +657,21 @@ static int make_map(CUtensorMap* map, const void* base, int esz, uint64_t X, uin
   return r == CUDA_SUCCESS ? FBST_OK : FBST_ERR_CUDA;
 }
 
+// 3-D map over the interleaved complex64 w [nblk][B][L] read as floats: dims {2L, B, nblk}, box
+// {32 floats, 1, boxZ}, no swizzle (the converter warps index it themselves).
+static int make_map_w(CUtensorMap* map, const void* base, uint64_t L2f, uint64_t B, uint64_t nblk, uint32_t boxZ) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return FBST_ERR_UNSUPPORTED;
+  const cuuint64_t dims[3] = {L2f, B, nblk};
+  const cuuint64_t strides[2] = {L2f * 4, L2f * B * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / 4), 1, boxZ};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? FBST_OK : FBST_ERR_CUDA;
+}
+
 template <int V>
 static size_t plane_bytes_G(const fbst_info& in) {
   return (size_t)in.B * tc_traits<V>::NPL * in.N * in.L * tc_traits<V>::ESZ;
@@ -439,12 +695,23 @@ static int build_operand_V(fbst_plan_s* p, cudaStream_t s) {
   return FBST_OK;
 }
 
+static int build_operand_fused(fbst_plan_s* p, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  if (in.L % 8 != 0) return FBST_ERR_UNSUPPORTED;
+  const size_t bytes = (size_t)in.B * 2 * in.N * in.L * sizeof(float);
+  FBST_CUDA_TRY(cudaMalloc(&p->Gtc, bytes));
+  p->Gtc_bytes = bytes;
+  k_tc_planes_f32<<<4096, 256, 0, s>>>(p->G, static_cast<float*>(p->Gtc), in.B, in.N, in.L);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
 int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s) {
   if (!tensor_map_encoder()) return FBST_ERR_UNSUPPORTED;
   switch (variant_of(p->info.stage2)) {
     case TC_BF16X3: return build_operand_V<TC_BF16X3>(p, s);
     case TC_TF32: return build_operand_V<TC_TF32>(p, s);
-    case TC_TF32X3: return build_operand_V<TC_TF32X3>(p, s);
+    case TC_TF32X3: return build_operand_fused(p, s);
     default: return FBST_ERR_INVALID;
   }
 }
@@ -486,13 +753,37 @@ static int launch_V(const fbst_plan_s* p, const float2* w, float2* bhat, int nbl
   return FBST_ERR_INVALID;
 }
 
+template <int NB>
+static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  CUtensorMap mapA, mapW;
+  int r = make_map(&mapA, p->Gtc, 4, in.L, in.N, (uint64_t)in.B * 2, kTileM);
+  if (r != FBST_OK) return r;
+  r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, in.B, nblk, NB);
+  if (r != FBST_OK) return r;
+  const int smem = fused_smem<NB>::BYTES;
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const dim3 grid((in.N + kTileM - 1) / kTileM, in.B, (nblk + NB - 1) / NB);
+  k_dense_tc_fused<NB><<<grid, 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk, p->d_status);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+static int launch_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  const int want = std::min(round16(nblk), 64);
+  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, s);
+  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, s);
+  return gemm_fused<64>(p, w, bhat, nblk, s);
+}
+
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
-  if (!p->Gtc || !p->ws_tc) return FBST_ERR_INVALID;
+  if (!p->Gtc) return FBST_ERR_INVALID;
+  if (variant_of(p->info.stage2) == TC_TF32X3) return launch_fused(p, w, bhat, nblk, s);
+  if (!p->ws_tc) return FBST_ERR_INVALID;
   switch (variant_of(p->info.stage2)) {
     case TC_BF16X3: return launch_V<TC_BF16X3>(p, w, bhat, nblk, s);
     case TC_TF32: return launch_V<TC_TF32>(p, w, bhat, nblk, s);
-    case TC_TF32X3: return launch_V<TC_TF32X3>(p, w, bhat, nblk, s);
     default: return FBST_ERR_INVALID;
   }
 }

@@ -245,7 +245,8 @@ int stage2_launches(const fbst_plan_s* p) {
     case FBST_STAGE2_GS:
     case FBST_STAGE2_GS_IR1: return 1;
     case FBST_STAGE2_DENSE_FP32: return 1;
-    default: return 2;  // tensor-core variants: operand preparation + GEMM
+    case FBST_STAGE2_DENSE_TF32X3: return 1;  // fused: splits its operands in shared memory
+    default: return 2;  // other tensor-core variants: operand preparation + GEMM
   }
 }
 
