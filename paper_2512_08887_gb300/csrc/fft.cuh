@@ -7,8 +7,8 @@
 // at stride P/R straight from registers, applies the twiddles exp(dir*2*pi*i*s*k/(Ns*R)) from an
 // FP64-built table, does a radix-R DFT in registers, and scatters its R outputs to shared memory in
 // Stockham order; after a barrier each thread reloads its E elements at stride T. R = E except for
-// a final smaller pass when P is not a power of E. Shared memory is padded by one element per 128
-// bytes so that the stride-R scatter of the early passes does not serialise on banks.
+// a final smaller pass when P is not a power of E. The exchange positions are XOR-swizzled per
+// pass (xpos below) so that neither the scatter nor the gather serialises on shared-memory banks.
 //
 // All threads of the CTA must call the same transform the same number of times (the passes use
 // __syncthreads()); several groups of T threads may run independent transforms of the same size
@@ -20,15 +20,27 @@
 
 namespace fbst {
 
-template <typename V> struct fft_pad {
-  // One padding element per 128 bytes.
-  static constexpr int shift = (sizeof(V) == 8) ? 4 : 3;
-  __device__ __forceinline__ static int at(int i) { return i + (i >> shift); }
-  static constexpr int words(int P) { return P + (P >> shift) + 1; }
-};
+// Shared-memory position of element i in the exchange of a pass with sub-transform size NS and
+// radix R, for a transform of size P. The low 4 bits of the index (an 8-byte element's bank within
+// a 128-byte row) are XORed with a key that is constant over every aligned run of 16 indices, so
+// the gather (t + T*r, consecutive over threads) stays conflict-free, and that separates the
+// groups of the scatter: the scatter of a pass writes base + s*NS with base = (j/NS)*NS*R + j%NS,
+// i.e. groups of NS consecutive threads NS*R apart. For NS*R >= 16 the key (j/NS)*NS spreads the
+// 16/NS groups of a half-warp over distinct banks; for NS*R < 16 (first passes, NS = 1) the row
+// index i >> 4 does. The map permutes each aligned block of 16, so no padding is needed.
+template <int P, int NS, int R>
+__device__ __forceinline__ int xpos(int i) {
+  if constexpr (P < 16) {
+    return i;
+  } else if constexpr (NS * R >= 16) {
+    return i ^ (((i / (NS * R)) * NS) & 15);
+  } else {
+    return i ^ ((i >> 4) & 15);
+  }
+}
 
 // Shared-memory elements one transform of size P needs.
-template <typename V> constexpr int fft_smem_elems(int P) { return fft_pad<V>::words(P); }
+template <typename V> constexpr int fft_smem_elems(int P) { return P; }
 
 // cos(2*pi*j/16), j = 0..15, for the in-register butterflies.
 __host__ __device__ constexpr double cos16(int j) {
@@ -94,7 +106,7 @@ __device__ __forceinline__ void dft(V* x) {
 }
 
 // One Stockham pass (current sub-transform size NS) followed by the remaining passes.
-// v[f][r] is element t + T*r of transform f; sbuf holds NF consecutive padded buffers.
+// v[f][r] is element t + T*r of transform f; sbuf holds NF consecutive buffers of P elements.
 template <int P, int E, int NF, int DIR, int NS, typename V>
 __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t) {
   if constexpr (NS < P) {
@@ -102,7 +114,7 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
     constexpr int T = P / E;
     constexpr int Q = E / R;                       // butterflies per thread in this pass
     constexpr int TW_STRIDE = kTwiddleSize / (NS * R);
-    constexpr int SB = fft_pad<V>::words(P);
+    constexpr int SB = fft_smem_elems<V>(P);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = t + T * q;                     // butterfly index, 0 <= j < P/R
@@ -137,14 +149,14 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
         }
         dft<R, DIR>(x);
 #pragma unroll
-        for (int s = 0; s < R; ++s) sbuf[f * SB + fft_pad<V>::at(base + s * NS)] = x[s];
+        for (int s = 0; s < R; ++s) sbuf[f * SB + xpos<P, NS, R>(base + s * NS)] = x[s];
       }
     }
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
 #pragma unroll
-      for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + fft_pad<V>::at(t + T * r)];
+      for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + xpos<P, NS, R>(t + T * r)];
     }
     __syncthreads();
     fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t);

@@ -21,7 +21,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
   extern __shared__ float2 sm[];
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   float2* fbuf = sm + g * SB;
-  float2* tile = sm + G * SB;  // [B][G]
+  float2* tile = sm + G * SB;  // [B][G + 1] (padded row: conflict-free column writes)
   long long it0, it1;
   my_range(jl.total, &it0, &it1);
   int j = 0, cur_j = -1, cur_lt = -1;
@@ -60,13 +60,13 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int b = t + T * r;
-      if (b < B) tile[b * G + g] = cmul(v[0][r], po[r]);
+      if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], po[r]);
     }
     __syncthreads();
     float2* out = J.w + (size_t)blk * B * L + ell0;
     for (int idx = threadIdx.x; idx < B * G; idx += blockDim.x) {
       const int b = idx / G, gg = idx % G;
-      if (ell0 + gg < L) out[(size_t)b * L + gg] = tile[idx];
+      if (ell0 + gg < L) out[(size_t)b * L + gg] = tile[b * (G + 1) + gg];
     }
     __syncthreads();
   }
@@ -75,7 +75,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 template <int P, int E, int G>
 static int run_space(const job_list<space_job>& jl, int max_B, const float2* tw, cudaStream_t s) {
   constexpr int T = P / E;
-  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * G);
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * (G + 1));
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
   FBST_TRY(allow_max_smem(k_czt_space_ula<P, E, G>));
   const int grid = grid_for_items(jl.total, resident_ctas(k_czt_space_ula<P, E, G>, G * T, smem));

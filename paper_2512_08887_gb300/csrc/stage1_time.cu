@@ -24,7 +24,7 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
   extern __shared__ float2 sm[];
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   float2* fbuf = sm + g * SB;
-  float2* tile = sm + G * SB;  // [Lh][G]
+  float2* tile = sm + G * SB;  // [Lh][G + 1] (padded row: conflict-free column writes)
   long long it0, it1;
   my_range(jl.total, &it0, &it1);
   int j = 0;
@@ -52,13 +52,13 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
-        if (i < Lh) tile[i * G + g] = cmul(u[0][r], J.post[h * Lh + i]);
+        if (i < Lh) tile[i * (G + 1) + g] = cmul(u[0][r], J.post[h * Lh + i]);
       }
       __syncthreads();
       float2* out = J.yhat + ((size_t)blk * L + (size_t)h * Lh) * M + m0;
       for (int idx = threadIdx.x; idx < Lh * G; idx += blockDim.x) {
         const int i = idx / G, gg = idx % G;
-        if (m0 + gg < M) out[(size_t)i * M + gg] = tile[idx];
+        if (m0 + gg < M) out[(size_t)i * M + gg] = tile[i * (G + 1) + gg];
       }
       __syncthreads();
     }
@@ -68,7 +68,7 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
 template <int P, int E, int G>
 static int run_time(const job_list<time_job>& jl, int max_Lh, const float2* tw, cudaStream_t s) {
   constexpr int T = P / E;
-  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_Lh * G);
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_Lh * (G + 1));
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
   FBST_TRY(allow_max_smem(k_czt_time<P, E, G>));
   const int grid = grid_for_items(jl.total, resident_ctas(k_czt_time<P, E, G>, G * T, smem));
