@@ -11,9 +11,9 @@
 //            hi*hi + hi*lo + lo*hi: FP32-class accuracy
 // always with FP32 accumulation in tensor memory.
 //
-// Long sums in TF32 lose accuracy as K = L grows, so the K chunks are spread over KACC partial
-// accumulators in tensor memory (chunk c adds into accumulator c % KACC, up to 4 of them within
-// the 512 columns) and the epilogue adds the partials in FP32.
+// Long sums in TF32 lose accuracy as K = L grows, so k_dense_tc spreads the K chunks over KACC
+// partial accumulators in tensor memory (chunk c adds into accumulator c % KACC, up to 4 of them
+// within the 512 columns) and the epilogue adds the partials in FP32.
 //
 // BF16X3 and TF32 (k_dense_tc: one CTA = one beam x 128 output samples x up to NB blocks, 128
 // threads) read operands that separate kernels have already split into planes:
@@ -22,12 +22,9 @@
 //   warp 1    : tensor-memory allocation / release (2 x NB columns per accumulator, KACC of them)
 //   warps 0-3 : epilogue (tcgen05.ld 32x32b, rows = samples, coalesced complex64 stores)
 // TF32X3 (k_dense_tc_fused, 256 threads) reads plain FP32 planes of G and the stage-1 output w as
-// it is (interleaved complex64) and splits both in shared memory, so no split pass goes through HBM:
-//   thread 0  : TMA producer (G planes with the 128-byte swizzle; raw w rows without swizzle)
-//   warp 1    : MMA issuer and tensor-memory owner
-//   warps 4-7 : converters: G and raw w -> TF32 hi / FP32 residual planes in the swizzled layout
-//               the MMA reads (cvt.rna.tf32), one mbarrier arrival per thread per stage
-//   warps 0-3 : epilogue as above
+// it is (interleaved complex64) and splits both on chip, so no split pass goes through HBM: the
+// split G goes to tensor memory (the MMA's A operand), the split w to shared memory with the real
+// and imaginary parts stacked along N, so each MMA is 128 x 2NB; see the kernel's own comment.
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel records FBST_ERR_TIMEOUT
 // in the plan's status word, waits (bounded) for its copies in flight, frees its tensor memory
 // and returns.
@@ -397,47 +394,88 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 }
 
 // ---------------------------------------------------------------------------------------------
-// Fused TF32x3 kernel: the plan keeps G_b as plain FP32 real/imaginary planes and the kernel reads
-// the interleaved complex64 w tiles straight from stage 1; a converter warpgroup splits both into
-// TF32 (hi, lo) planes in shared memory before the MMA thread consumes them. Compared with
-// pre-split operands this halves the bytes of G and removes the W preparation pass.
-//   warp 0 lane 0 : TMA producer      warp 1 lane 0 : MMA issuer (+ warp 1 TMEM alloc/free)
-//   warps 4-7     : converters        warps 0-3     : epilogue
+// Fused TF32x3 kernel. The plan keeps G_b as plain FP32 real/imaginary planes; the kernel reads
+// them and the interleaved complex64 w tiles of stage 1 straight by TMA and splits both on chip:
+//   * G (the MMA's A operand) goes to tensor memory: for every K step of 8 values a converter
+//     thread owns one row, rounds it to TF32 (hi) and keeps the FP32 residual (lo), and stores
+//     [hi_re | hi_im | lo_re | lo_im] (4 x 8 columns) into a ring of 4 tensor-memory slots with
+//     tcgen05.st. The MMAs take A from tensor memory, so shared memory only feeds B.
+//   * w (the B operand) is deinterleaved into two stacked planes per stage, hi and lo, each of
+//     3*NB rows [-W_im | W_re | W_im] in the 128-byte swizzle layout. Rows NB..3NB are
+//     [W_re | W_im] and rows 0..2NB are [-W_im | W_re], so one MMA of N = 2*NB gives
+//     A_re [W_re | W_im] and another A_im [-W_im | W_re]; their sum is [C_re | C_im]. (Two MMAs of
+//     N = NB with the negate-B bit instead need a smaller plane but run slower per MAC.)
+// Per K step: 2 MMAs of hi*hi into accumulator H[chunk parity] and 4 of hi*lo / lo*hi into
+// accumulator LO (terms 2^-11 smaller, so their rounding does not matter); the epilogue adds
+// H0 + H1 + LO in FP32. Splitting the large hi*hi sum over two accumulators keeps the growth of
+// the accumulation error with L in check.
+// The converters copy a chunk's G rows to registers and release its raw TMA stage before they
+// wait for tensor-memory slots, so the next TMA load is not held up by the MMAs.
+//   thread 0   : TMA producer (raw stage ring, freed by the converters once read)
+//   thread 32  : MMA issuer; warp 1 allocates and frees tensor memory
+//   warps 4-7  : converters (thread = A row = tensor-memory lane)
+//   warps 0-3  : epilogue (tcgen05.ld, FP32 sums, coalesced complex64 stores)
 // ---------------------------------------------------------------------------------------------
 template <int NB>
 struct fused_smem {
-  static constexpr int STAGES = 2;
-  static constexpr int A_TILE = kTileM * kRowBytes;    // one 128-row plane of 32 FP32 values per row
-  static constexpr int B_TILE = NB * kRowBytes;
-  static constexpr int WRAW_OFF = 4 * A_TILE;          // A planes: re_hi, im_hi (TMA, split in place), re_lo, im_lo
-  static constexpr int WPL_OFF = WRAW_OFF + 2 * B_TILE; // two raw interleaved w boxes (16 complex per row each)
-  static constexpr int STAGE_BYTES = WPL_OFF + 4 * B_TILE;  // W planes: re_hi, re_lo, im_hi, im_lo
-  static constexpr int TMA_BYTES = 2 * A_TILE + 2 * B_TILE;
-  static constexpr int BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int RAW_STAGES = 2, PL_STAGES = 2;
+  static constexpr int A_TILE = kTileM * kRowBytes;         // one FP32 plane of G: 128 rows x 32 K values
+  static constexpr int W_BOX = NB * kRowBytes;              // raw w: NB rows x 16 complex values
+  static constexpr int RAW_BYTES = 2 * A_TILE + 2 * W_BOX;  // TMA bytes of one stage (re, im, 2 w boxes)
+  static constexpr int WPL = 3 * NB * kRowBytes;            // one stacked plane [-W_im | W_re | W_im]
+  static constexpr int PL_OFF = RAW_STAGES * RAW_BYTES;     // W planes: PL_STAGES x {hi, lo}
+  static constexpr int BAR_OFF = PL_OFF + PL_STAGES * 2 * WPL;
+  static constexpr int BYTES = BAR_OFF + 256 + 1024;        // barriers + alignment slack
+  static_assert(RAW_BYTES % 1024 == 0 && WPL % 1024 == 0, "1024-byte aligned swizzle atoms");
+  static_assert(BYTES <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ float4 rna4(float4 x) {
   return make_float4(round_tf32(x.x), round_tf32(x.y), round_tf32(x.z), round_tf32(x.w));
 }
 __device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 neg4(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+
+// TF32 MMA with A in tensor memory, B from a shared-memory descriptor.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// 16 consecutive 32-bit columns of this warp's 32 lanes (one value per thread and column).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
 
 template <int NB>
 __global__ void __launch_bounds__(256, 1)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
   using SM = fused_smem<NB>;
-  constexpr int STAGES = SM::STAGES;
-  constexpr int KELEM = kRowBytes / 4;   // 32 FP32 values of K per chunk
-  constexpr int KSTEPS = kRowBytes / 32; // MMAs of K = 8 per chunk
-  constexpr int KACC = 2 * NB * 4 <= 512 ? 4 : (2 * NB * 2 <= 512 ? 2 : 1);
-  constexpr uint32_t COLS = 2 * NB * KACC;
-  constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+  constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
+  constexpr int KELEM = kRowBytes / 4;  // 32 FP32 values of K per chunk
+  constexpr int KSTEPS = KELEM / 8;     // MMAs of K = 8 per chunk and term
+  constexpr uint32_t RING = 0, H0 = 32 * KSTEPS, H1 = H0 + 2 * NB, LO = H1 + 2 * NB;
+  constexpr uint32_t COLS = LO + 2 * NB;
+  constexpr uint32_t TMEM_COLS = COLS <= 256 ? 256 : 512;
+  static_assert(COLS <= 512, "tensor memory holds 512 columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * SM::STAGE_BYTES);
-  uint64_t* conv = full + STAGES;
-  uint64_t* empty = conv + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SM::BAR_OFF);
+  uint64_t* rawfree = full + RS;
+  uint64_t* wconv = rawfree + RS;
+  uint64_t* wfree = wconv + PS;
+  uint64_t* aready = wfree + PS;
+  uint64_t* afree = aready + KSTEPS;
+  uint64_t* done = afree + KSTEPS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -446,10 +484,17 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int nchunks = (L + KELEM - 1) / KELEM;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < RS; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
-      mbar_init(&empty[s], 1);
+      mbar_init(&rawfree[s], 128);
+    }
+    for (int s = 0; s < PS; ++s) {
+      mbar_init(&wconv[s], 128);
+      mbar_init(&wfree[s], 1);
+    }
+    for (int k = 0; k < KSTEPS; ++k) {
+      mbar_init(&aready[k], 128);
+      mbar_init(&afree[k], 1);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -471,104 +516,146 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     // ---------------- TMA producer ----------------
     int issued = 0;
     for (int c = 0; c < nchunks; ++c) {
-      const int s = c % STAGES;
-      if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) {
+      const int s = c % RS;
+      if (c >= RS && !mbar_wait(&rawfree[s], ((c / RS) - 1) & 1)) {
         atomicExch(status, (int)FBST_ERR_TIMEOUT);
         *abort_flag = 1;
         break;
       }
       if (*abort_flag) break;
-      uint8_t* st = smem + s * SM::STAGE_BYTES;
-      mbar_expect_tx(&full[s], SM::TMA_BYTES);
+      uint8_t* st = smem + s * SM::RAW_BYTES;
+      mbar_expect_tx(&full[s], SM::RAW_BYTES);
       tma_load_3d(st, &mapA, &full[s], c * KELEM, m0, b * 2 + 0);
       tma_load_3d(st + SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * 2 + 1);
-      tma_load_3d(st + SM::WRAW_OFF, &mapW, &full[s], 2 * c * KELEM, b, blk0);
-      tma_load_3d(st + SM::WRAW_OFF + SM::B_TILE, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
+      tma_load_3d(st + 2 * SM::A_TILE, &mapW, &full[s], 2 * c * KELEM, b, blk0);
+      tma_load_3d(st + 2 * SM::A_TILE + SM::W_BOX, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
       issued = c + 1;
     }
     if (*abort_flag) {
-      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
-        (void)mbar_wait(&full[c % STAGES], (c / STAGES) & 1);
+      for (int c = (issued > RS ? issued - RS : 0); c < issued; ++c) (void)mbar_wait(&full[c % RS], (c / RS) & 1);
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t ID_POS = make_idesc(2u, kTileM, NB, false);
-    constexpr uint32_t ID_NEG = make_idesc(2u, kTileM, NB, true);
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % STAGES;
-      if (!mbar_wait(&conv[s], (c / STAGES) & 1)) {
-        atomicExch(status, (int)FBST_ERR_TIMEOUT);
-        *abort_flag = 1;
+    constexpr uint32_t ID = make_idesc(2u, kTileM, 2 * NB, false);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int ps = c % PS;
+      if (!mbar_wait(&wconv[ps], (c / PS) & 1)) {
+        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(smem + s * SM::STAGE_BYTES);
-      const uint32_t d_re = tmem + (uint32_t)((c % KACC) * 2 * NB), d_im = d_re + NB;
-      constexpr int ARH = 0, AIH = 1, ARL = 2, AIL = 3;  // A planes
-      constexpr int WRH = 0, WRL = 1, WIH = 2, WIL = 3;  // W planes
+      const uint32_t bh = smem_u32(smem + SM::PL_OFF + ps * 2 * SM::WPL), bl = bh + SM::WPL;
+      const uint32_t hacc = tmem + ((c & 1) ? H1 : H0), lacc = tmem + LO;
 #pragma unroll
       for (int k = 0; k < KSTEPS; ++k) {
-        auto da = [&](int pl) { return smem_desc_sw128(st + pl * SM::A_TILE + k * 32); };
-        auto db = [&](int pl) { return smem_desc_sw128(st + SM::WPL_OFF + pl * SM::B_TILE + k * 32); };
-        const uint32_t acc0 = (c >= KACC || k > 0) ? 1u : 0u;
-        // C_re = G_re W_re - G_im W_im ; C_im = G_re W_im + G_im W_re ; each as hi*hi + hi*lo + lo*hi
-        mma_issue<TC_TF32X3>(d_re, da(ARH), db(WRH), ID_POS, acc0);
-        mma_issue<TC_TF32X3>(d_re, da(AIH), db(WIH), ID_NEG, 1u);
-        mma_issue<TC_TF32X3>(d_im, da(ARH), db(WIH), ID_POS, acc0);
-        mma_issue<TC_TF32X3>(d_im, da(AIH), db(WRH), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_re, da(ARH), db(WRL), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_re, da(ARL), db(WRH), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_re, da(AIH), db(WIL), ID_NEG, 1u);
-        mma_issue<TC_TF32X3>(d_re, da(AIL), db(WIH), ID_NEG, 1u);
-        mma_issue<TC_TF32X3>(d_im, da(ARH), db(WIL), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_im, da(ARL), db(WIH), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_im, da(AIH), db(WRL), ID_POS, 1u);
-        mma_issue<TC_TF32X3>(d_im, da(AIL), db(WRH), ID_POS, 1u);
+        if (!mbar_wait(&aready[k], c & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a = tmem + RING + 32 * k;  // [hi_re | hi_im | lo_re | lo_im], 8 columns each
+        // rows NB..3NB = [W_re | W_im] and rows 0..2NB = [-W_im | W_re] of the hi and lo planes
+        const uint64_t h1 = smem_desc_sw128(bh + NB * kRowBytes + k * 32), h2 = smem_desc_sw128(bh + k * 32);
+        const uint64_t l1 = smem_desc_sw128(bl + NB * kRowBytes + k * 32), l2 = smem_desc_sw128(bl + k * 32);
+        const uint32_t hfirst = (c < 2 && k == 0) ? 0u : 1u, lfirst = (c == 0 && k == 0) ? 0u : 1u;
+        mma_tf32_ts(hacc, a + 0, h1, ID, hfirst);  // hi_re x [W_re | W_im]_hi
+        mma_tf32_ts(hacc, a + 8, h2, ID, 1u);      // hi_im x [-W_im | W_re]_hi
+        mma_tf32_ts(lacc, a + 0, l1, ID, lfirst);  // hi_re x lo
+        mma_tf32_ts(lacc, a + 8, l2, ID, 1u);      // hi_im x lo
+        mma_tf32_ts(lacc, a + 16, h1, ID, 1u);     // lo_re x hi
+        mma_tf32_ts(lacc, a + 24, h2, ID, 1u);     // lo_im x hi
+        mma_commit(&afree[k]);
       }
-      mma_commit(&empty[s]);
+      if (ok) mma_commit(&wfree[ps]);
+    }
+    if (!ok) {
+      atomicExch(status, (int)FBST_ERR_TIMEOUT);
+      *abort_flag = 1;
     }
     mma_commit(done);
   } else if (warp >= 4) {
     // ---------------- converters ----------------
-    const int ct = threadIdx.x - 128;
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % STAGES;
-      if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
-        atomicExch(status, (int)FBST_ERR_TIMEOUT);
-        *abort_flag = 1;
+    const int ct = threadIdx.x - 128;  // A row and tensor-memory lane
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c % RS, ps = c % PS;
+      if (!mbar_wait(&full[s], (c / RS) & 1)) {
+        ok = false;
         break;
       }
-      uint8_t* st = smem + s * SM::STAGE_BYTES;
-      // A: split each FP32 value into TF32 hi (in place) and the FP32 remainder (lo plane); the
-      // operation is elementwise, so the swizzled positions carry over unchanged.
-#pragma unroll 4
-      for (int i = ct; i < 2 * kTileM * 8; i += 128) {
-        const int pl = i / (kTileM * 8), off = (i % (kTileM * 8)) * 16;
-        float4* hp = reinterpret_cast<float4*>(st + pl * SM::A_TILE + off);
-        const float4 x = *hp;
-        const float4 hi = rna4(x);
-        *hp = hi;
-        *reinterpret_cast<float4*>(st + (2 + pl) * SM::A_TILE + off) = sub4(x, hi);
+      const uint8_t* raw = smem + s * SM::RAW_BYTES;
+      // This thread's row of G for the whole chunk: 16-byte chunk j of row ct sits at j ^ (ct & 7).
+      float4 ar[2 * KSTEPS], ai[2 * KSTEPS];
+#pragma unroll
+      for (int j = 0; j < 2 * KSTEPS; ++j) {
+        const int off = ct * kRowBytes + ((j ^ (ct & 7)) << 4);
+        ar[j] = *reinterpret_cast<const float4*>(raw + off);
+        ai[j] = *reinterpret_cast<const float4*>(raw + SM::A_TILE + off);
       }
-      // W: deinterleave 4 complex values (two raw 16-byte chunks) into one 16-byte chunk of each of
-      // the four planes, at the 128-byte-swizzled position of (row r, chunk q).
+      if (c >= PS && !mbar_wait(&wfree[ps], ((c / PS) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      uint8_t* ph = smem + SM::PL_OFF + ps * 2 * SM::WPL;
+      // B: 4 complex values (32 raw bytes) -> one 16-byte chunk (row r, chunk q) of the -W_im, W_re
+      // and W_im rows of both planes, at the swizzled position. The two raw halves are read in an
+      // order that depends on the box, so the 8 threads of one row touch 8 different bank groups.
 #pragma unroll 2
       for (int j = ct; j < NB * 8; j += 128) {
-        const int r = j >> 3, q = j & 7;
-        const uint8_t* raw = st + SM::WRAW_OFF + (q >> 2) * SM::B_TILE + r * kRowBytes + (q & 3) * 32;
-        const float4 a = *reinterpret_cast<const float4*>(raw);
-        const float4 bb = *reinterpret_cast<const float4*>(raw + 16);
+        const int r = j >> 3, q = j & 7, box = q >> 2;
+        const uint8_t* rp = raw + 2 * SM::A_TILE + box * SM::W_BOX + r * kRowBytes + (q & 3) * 32;
+        const float4 x0 = *reinterpret_cast<const float4*>(rp + 16 * box);
+        const float4 x1 = *reinterpret_cast<const float4*>(rp + 16 * (1 - box));
+        const float4 a = box ? x1 : x0, bb = box ? x0 : x1;
         const float4 re = make_float4(a.x, a.z, bb.x, bb.z), im = make_float4(a.y, a.w, bb.y, bb.w);
-        const float4 rh = rna4(re), ih = rna4(im);
+        const float4 rh = rna4(re), ih = rna4(im), rl = sub4(re, rh), il = sub4(im, ih);
         const int off = r * kRowBytes + ((q ^ (r & 7)) << 4);
-        uint8_t* wp = st + SM::WPL_OFF + off;
-        *reinterpret_cast<float4*>(wp + 0 * SM::B_TILE) = rh;
-        *reinterpret_cast<float4*>(wp + 1 * SM::B_TILE) = sub4(re, rh);
-        *reinterpret_cast<float4*>(wp + 2 * SM::B_TILE) = ih;
-        *reinterpret_cast<float4*>(wp + 3 * SM::B_TILE) = sub4(im, ih);
+        uint8_t* hp = ph + off;
+        uint8_t* lp = ph + SM::WPL + off;
+        *reinterpret_cast<float4*>(hp) = neg4(ih);
+        *reinterpret_cast<float4*>(hp + NB * kRowBytes) = rh;
+        *reinterpret_cast<float4*>(hp + 2 * NB * kRowBytes) = ih;
+        *reinterpret_cast<float4*>(lp) = neg4(il);
+        *reinterpret_cast<float4*>(lp + NB * kRowBytes) = rl;
+        *reinterpret_cast<float4*>(lp + 2 * NB * kRowBytes) = il;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&wconv[ps])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&rawfree[s])) : "memory");
+      // A: split each K step into tensor-memory slot k once the MMAs of the previous chunk freed it.
+#pragma unroll
+      for (int k = 0; k < KSTEPS; ++k) {
+        const float x[2][8] = {{ar[2 * k].x, ar[2 * k].y, ar[2 * k].z, ar[2 * k].w, ar[2 * k + 1].x, ar[2 * k + 1].y,
+                                ar[2 * k + 1].z, ar[2 * k + 1].w},
+                               {ai[2 * k].x, ai[2 * k].y, ai[2 * k].z, ai[2 * k].w, ai[2 * k + 1].x, ai[2 * k + 1].y,
+                                ai[2 * k + 1].z, ai[2 * k + 1].w}};
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float h = round_tf32(x[e][i]);
+            hi[e * 8 + i] = __float_as_uint(h);
+            lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
+          }
+        }
+        if (c >= 1 && !mbar_wait(&afree[k], (c - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_st16(lane_addr + RING + 32 * k, hi);
+        tmem_st16(lane_addr + RING + 32 * k + 16, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aready[k])) : "memory");
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicExch(status, (int)FBST_ERR_TIMEOUT);
+      *abort_flag = 1;
     }
   }
   __syncwarp();
@@ -582,26 +669,28 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int n = m0 + warp * 32 + lane;
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-      const int nacc = nchunks < KACC ? nchunks : KACC;
+      const bool two = nchunks >= 2;
 #pragma unroll 1
       for (int j0 = 0; j0 < NB; j0 += 16) {
-        float re[16], im[16];
-        tmem_ld16(lane_base + j0, re);
-        tmem_ld16(lane_base + NB + j0, im);
-        for (int q = 1; q < nacc; ++q) {
-          float re2[16], im2[16];
-          tmem_ld16(lane_base + q * 2 * NB + j0, re2);
-          tmem_ld16(lane_base + q * 2 * NB + NB + j0, im2);
+        float re[16], im[16], t0[16], t1[16];
+        tmem_ld16(lane_base + H0 + j0, re);
+        tmem_ld16(lane_base + H0 + NB + j0, im);
+        tmem_ld16(lane_base + LO + j0, t0);
+        tmem_ld16(lane_base + LO + NB + j0, t1);
+        if (two) {
+          float u0[16], u1[16];
+          tmem_ld16(lane_base + H1 + j0, u0);
+          tmem_ld16(lane_base + H1 + NB + j0, u1);
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            re[jj] += re2[jj];
-            im[jj] += im2[jj];
+            re[jj] += u0[jj];
+            im[jj] += u1[jj];
           }
         }
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int blk = blk0 + j0 + jj;
-          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj], im[jj]);
+          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj] + t0[jj], im[jj] + t1[jj]);
         }
       }
     }
