@@ -9,11 +9,15 @@
 // Stockham order; after a barrier each thread reloads its E elements at stride T. R = E except for
 // a final smaller pass when P is not a power of E. The exchange positions are XOR-swizzled per
 // pass (xpos below) so that neither the scatter nor the gather serialises on shared-memory banks.
+// The last pass needs no exchange: its Stockham positions are t + T*(q + Q*s), the thread's own
+// slots, so its outputs stay in registers (a transform of p passes makes p - 1 exchanges).
 //
 // All threads of the CTA must call the same transform the same number of times (the passes use
 // __syncthreads()); several groups of T threads may run independent transforms of the same size
-// in lockstep, each on its own shared buffer. Inverse transforms are not normalised: every
-// 1/P factor is folded into the plan's tables.
+// in lockstep, each on its own shared buffer. Every call executes at least one barrier, and its
+// last shared-memory access precedes its last barrier, so a caller may reuse the buffer (or any
+// other shared memory read before the call) right after it returns. Inverse transforms are not
+// normalised: every 1/P factor is folded into the plan's tables.
 #pragma once
 
 #include "common.cuh"
@@ -148,18 +152,28 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
           for (int s = 1; s < R; ++s) x[s] = cmul(x[s], w[s]);
         }
         dft<R, DIR>(x);
+        if constexpr (NS * R == P) {
+          // Last pass: output s lands at base + s*NS = t + T*(q + Q*s), this thread's slot q + Q*s.
 #pragma unroll
-        for (int s = 0; s < R; ++s) sbuf[f * SB + xpos<P, NS, R>(base + s * NS)] = x[s];
+          for (int s = 0; s < R; ++s) v[f][q + Q * s] = x[s];
+        } else {
+#pragma unroll
+          for (int s = 0; s < R; ++s) sbuf[f * SB + xpos<P, NS, R>(base + s * NS)] = x[s];
+        }
       }
     }
-    __syncthreads();
+    if constexpr (NS * R == P) {
+      if constexpr (NS == 1) __syncthreads();  // single-pass transform: keep one barrier per call
+    } else {
+      __syncthreads();
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NF; ++f) {
 #pragma unroll
-      for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + xpos<P, NS, R>(t + T * r)];
+        for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + xpos<P, NS, R>(t + T * r)];
+      }
+      __syncthreads();
+      fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t);
     }
-    __syncthreads();
-    fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t);
   }
 }
 
