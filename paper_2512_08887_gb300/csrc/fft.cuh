@@ -12,12 +12,15 @@
 // The last pass needs no exchange: its Stockham positions are t + T*(q + Q*s), the thread's own
 // slots, so its outputs stay in registers (a transform of p passes makes p - 1 exchanges).
 //
-// All threads of the CTA must call the same transform the same number of times (the passes use
-// __syncthreads()); several groups of T threads may run independent transforms of the same size
-// in lockstep, each on its own shared buffer. Every call executes at least one barrier, and its
-// last shared-memory access precedes its last barrier, so a caller may reuse the buffer (or any
-// other shared memory read before the call) right after it returns. Inverse transforms are not
-// normalised: every 1/P factor is folded into the plan's tables.
+// All threads of a group of T threads must call the same transform the same number of times;
+// several groups may run independent transforms of the same size, each on its own shared buffer.
+// The passes synchronise with __syncthreads() (bar = 0: all threads of the CTA call the transform)
+// or, with bar = 1 + group index, only among the group's T threads (a named barrier, or a warp
+// barrier when the group lies inside one warp), so groups do not wait for each other. Every call
+// executes at least one such barrier, and its last shared-memory access precedes its last barrier,
+// so the threads it synchronises may reuse the buffer (or any other shared memory they read before
+// the call) right after it returns. Inverse transforms are not normalised: every 1/P factor is
+// folded into the plan's tables.
 #pragma once
 
 #include "common.cuh"
@@ -40,6 +43,19 @@ __device__ __forceinline__ int xpos(int i) {
     return i ^ (((i / (NS * R)) * NS) & 15);
   } else {
     return i ^ ((i >> 4) & 15);
+  }
+}
+
+// Barrier of the transform's threads: the CTA (bar = 0) or the group of T threads that owns
+// barrier id bar (T a multiple of 32), or its warp (T <= 32).
+template <int T>
+__device__ __forceinline__ void fft_sync(int bar) {
+  if (bar == 0) {
+    __syncthreads();
+  } else if constexpr (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(T) : "memory");
   }
 }
 
@@ -112,7 +128,7 @@ __device__ __forceinline__ void dft(V* x) {
 // One Stockham pass (current sub-transform size NS) followed by the remaining passes.
 // v[f][r] is element t + T*r of transform f; sbuf holds NF consecutive buffers of P elements.
 template <int P, int E, int NF, int DIR, int NS, typename V>
-__device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t) {
+__device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t, int bar) {
   if constexpr (NS < P) {
     constexpr int R = (P / NS < E) ? (P / NS) : E;
     constexpr int T = P / E;
@@ -163,27 +179,29 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
       }
     }
     if constexpr (NS * R == P) {
-      if constexpr (NS == 1) __syncthreads();  // single-pass transform: keep one barrier per call
+      if constexpr (NS == 1) fft_sync<T>(bar);  // single-pass transform: keep one barrier per call
     } else {
-      __syncthreads();
+      fft_sync<T>(bar);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
 #pragma unroll
         for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + xpos<P, NS, R>(t + T * r)];
       }
-      __syncthreads();
-      fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t);
+      fft_sync<T>(bar);
+      fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t, bar);
     }
   }
 }
 
 // NF simultaneous transforms of size P in the strided register layout described above.
 // DIR = -1: forward (exp(-i...)); DIR = +1: unnormalised inverse. sbuf: NF*fft_smem_elems(P).
+// bar: 0 for CTA-wide barriers, else 1 + the group index (1..15) of a group of P/E threads.
 template <int P, int E, int NF, int DIR, typename V>
-__device__ __forceinline__ void block_fft(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t) {
+__device__ __forceinline__ void block_fft(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t, int bar = 0) {
   static_assert((P & (P - 1)) == 0 && P >= 2 && P <= kMaxFFT, "P must be a power of two <= 4096");
   static_assert(E >= 2 && E <= 16 && (E & (E - 1)) == 0 && E <= P, "E must be a power of two <= 16");
-  fft_passes<P, E, NF, DIR, 1>(v, sbuf, tw, t);
+  static_assert(P / E <= 32 || (P / E) % 32 == 0, "a group barrier spans whole warps");
+  fft_passes<P, E, NF, DIR, 1>(v, sbuf, tw, t, bar);
 }
 
 }  // namespace fbst

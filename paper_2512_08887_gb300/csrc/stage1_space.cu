@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(G * (P / E))
 k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __restrict__ tw) {
   constexpr int T = P / E;
   constexpr int SB = fft_smem_elems<float2>(P);
+  static_assert(T <= 32 || G <= 15, "named barriers 1..15, one per transform group");
   extern __shared__ float2 sm[];
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   float2* fbuf = sm + g * SB;
@@ -53,10 +54,10 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
       const int i = t + T * r;
       v[0][r] = i < M ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
     }
-    block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+    block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
     for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], ks[r]);
-    block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+    block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int b = t + T * r;
@@ -141,6 +142,7 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
   constexpr int T = P / E;
   constexpr int G = NTH / T;  // concurrent transforms
   constexpr int SB = fft_smem_elems<float2>(P);
+  static_assert(T <= 32 || G <= 15, "named barriers 1..15, one per transform group");
   extern __shared__ float2 sm[];
   const int mx = axx.Ma, bx = axx.Ba, my = axy.Ma, by = axy.Ba;
   const int M = mx * my, B = bx * by;
@@ -166,10 +168,10 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
           const int ky = t + T * r;
           v[0][r] = (act && ky < my) ? cmul(src[kx * my + ky], axy.pre[(size_t)ell * my + ky]) : make_float2(0.f, 0.f);
         }
-        block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+        block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
         for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], axy.kspec[(size_t)ell * P + t + T * r]);
-        block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+        block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int c = t + T * r;
@@ -186,10 +188,10 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
           const int kx = t + T * r;
           v[0][r] = (act && kx < mx) ? cmul(Z[kx * by + c], axx.pre[(size_t)ell * mx + kx]) : make_float2(0.f, 0.f);
         }
-        block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+        block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
         for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], axx.kspec[(size_t)ell * P + t + T * r]);
-        block_fft<P, E, 1, +1>(v, fbuf, tw, t);
+        block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int a = t + T * r;

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(G * (P / E))
 k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restrict__ tw) {
   constexpr int T = P / E;
   constexpr int SB = fft_smem_elems<float2>(P);
+  static_assert(T <= 32 || G <= 15, "named barriers 1..15, one per transform group");
   extern __shared__ float2 sm[];
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   float2* fbuf = sm + g * SB;
@@ -43,12 +44,12 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
       const int n = t + T * r;
       v[0][r] = (n < N && m < M) ? cmul(yrow[n], J.pre[n]) : make_float2(0.f, 0.f);
     }
-    block_fft<P, E, 1, -1>(v, fbuf, tw, t);
+    block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
     for (int h = 0; h < S; ++h) {
       float2 u[1][E];
 #pragma unroll
       for (int r = 0; r < E; ++r) u[0][r] = cmul(v[0][r], J.gspec[h * P + t + T * r]);
-      block_fft<P, E, 1, +1>(u, fbuf, tw, t);
+      block_fft<P, E, 1, +1>(u, fbuf, tw, t, 1 + g);
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
