@@ -21,7 +21,7 @@
 //   thread 32 : MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = NB, K = 32 bytes per step)
 //   warp 1    : tensor-memory allocation / release (2 x NB columns per accumulator, KACC of them)
 //   warps 0-3 : epilogue (tcgen05.ld 32x32b, rows = samples, coalesced complex64 stores)
-// TF32X3 (k_dense_tc_fused, 256 threads) reads plain FP32 planes of G and the stage-1 output w as
+// TF32X3 (k_dense_tc_fused, 384 threads) reads plain FP32 planes of G and the stage-1 output w as
 // it is (interleaved complex64) and splits both on chip, so no split pass goes through HBM: the
 // split G goes to tensor memory (the MMA's A operand), the split w to shared memory with the real
 // and imaginary parts stacked along N, so each MMA is 128 x 2NB; see the kernel's own comment.
@@ -32,9 +32,11 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <climits>
 #include <mutex>
 
 #include "common.cuh"
+#include "launch_util.cuh"
 
 namespace fbst {
 
@@ -165,6 +167,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// The same load without the wait: several loads may be in flight before one tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
@@ -363,8 +375,8 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int n = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
     const int nacc = nchunks < KACC ? nchunks : KACC;
+#pragma unroll 1
     for (int j0 = 0; j0 < NB; j0 += 16) {
       float re[16], im[16];
       tmem_ld16(lane_base + j0, re);
@@ -411,10 +423,15 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 // the accumulation error with L in check.
 // The converters copy a chunk's G rows to registers and release its raw TMA stage before they
 // wait for tensor-memory slots, so the next TMA load is not held up by the MMAs.
+// The kernel is persistent: one CTA per SM walks tiles (beam x 128 samples x up to NB blocks)
+// with stride gridDim.x; the TMA, conversion and tensor-memory rings run on across tiles, and the
+// epilogue warps release the accumulators (tempty) as soon as they have read them, so the next
+// tile's loads and conversions overlap the previous tile's MMAs and stores.
 //   thread 0   : TMA producer (raw stage ring, freed by the converters once read)
 //   thread 32  : MMA issuer; warp 1 allocates and frees tensor memory
 //   warps 4-7  : converters (thread = A row = tensor-memory lane)
-//   warps 0-3  : epilogue (tcgen05.ld, FP32 sums, coalesced complex64 stores)
+//   warps 8-11 : epilogue (tcgen05.ld, FP32 sums, coalesced complex64 stores)
+//   warps 2-3  : idle
 // ---------------------------------------------------------------------------------------------
 template <int NB>
 struct fused_smem {
@@ -456,7 +473,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
   using SM = fused_smem<NB>;
@@ -475,13 +492,22 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   uint64_t* wfree = wconv + PS;
   uint64_t* aready = wfree + PS;
   uint64_t* afree = aready + KSTEPS;
-  uint64_t* done = afree + KSTEPS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = afree + KSTEPS;  // a tile's accumulators are complete
+  uint64_t* tempty = tfull + 1;      // the epilogue has read them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTileM, b = blockIdx.y, blk0 = blockIdx.z * NB;
   const int nchunks = (L + KELEM - 1) / KELEM;
+  const int mtiles = (N + kTileM - 1) / kTileM, ntiles = mtiles * B * ((nblk + NB - 1) / NB);
+  // Tile ti: row tile ti % mtiles, beam (ti / mtiles) % B, block group ti / (mtiles B). This CTA
+  // takes ti = blockIdx.x, blockIdx.x + gridDim.x, ...; every role walks the same sequence, and the
+  // chunk counter gc runs on across tiles, so the rings never drain between tiles.
+  auto tile_of = [&](int ti, int& m0, int& b, int& blk0) {
+    m0 = (ti % mtiles) * kTileM;
+    b = (ti / mtiles) % B;
+    blk0 = (ti / (mtiles * B)) * NB;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < RS; ++s) {
@@ -496,7 +522,8 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       mbar_init(&aready[k], 128);
       mbar_init(&afree[k], 1);
     }
-    mbar_init(done, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -514,178 +541,210 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 
   if (threadIdx.x == 0) {
     // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % RS;
-      if (c >= RS && !mbar_wait(&rawfree[s], ((c / RS) - 1) & 1)) {
-        atomicExch(status, (int)FBST_ERR_TIMEOUT);
-        *abort_flag = 1;
-        break;
-      }
-      if (*abort_flag) break;
-      uint8_t* st = smem + s * SM::RAW_BYTES;
-      mbar_expect_tx(&full[s], SM::RAW_BYTES);
-      tma_load_3d(st, &mapA, &full[s], c * KELEM, m0, b * 2 + 0);
-      tma_load_3d(st + SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * 2 + 1);
-      tma_load_3d(st + 2 * SM::A_TILE, &mapW, &full[s], 2 * c * KELEM, b, blk0);
-      tma_load_3d(st + 2 * SM::A_TILE + SM::W_BOX, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
-      issued = c + 1;
-    }
-    if (*abort_flag) {
-      for (int c = (issued > RS ? issued - RS : 0); c < issued; ++c) (void)mbar_wait(&full[c % RS], (c / RS) & 1);
-    }
-  } else if (threadIdx.x == 32) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t ID = make_idesc(2u, kTileM, 2 * NB, false);
+    int gc = 0, issued = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int ps = c % PS;
-      if (!mbar_wait(&wconv[ps], (c / PS) & 1)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t bh = smem_u32(smem + SM::PL_OFF + ps * 2 * SM::WPL), bl = bh + SM::WPL;
-      const uint32_t hacc = tmem + ((c & 1) ? H1 : H0), lacc = tmem + LO;
-#pragma unroll
-      for (int k = 0; k < KSTEPS; ++k) {
-        if (!mbar_wait(&aready[k], c & 1)) {
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      int m0, b, blk0;
+      tile_of(ti, m0, b, blk0);
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int s = gc % RS;
+        if ((gc >= RS && !mbar_wait(&rawfree[s], ((gc / RS) - 1) & 1)) || *abort_flag) {
           ok = false;
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a = tmem + RING + 32 * k;  // [hi_re | hi_im | lo_re | lo_im], 8 columns each
-        // rows NB..3NB = [W_re | W_im] and rows 0..2NB = [-W_im | W_re] of the hi and lo planes
-        const uint64_t h1 = smem_desc_sw128(bh + NB * kRowBytes + k * 32), h2 = smem_desc_sw128(bh + k * 32);
-        const uint64_t l1 = smem_desc_sw128(bl + NB * kRowBytes + k * 32), l2 = smem_desc_sw128(bl + k * 32);
-        const uint32_t hfirst = (c < 2 && k == 0) ? 0u : 1u, lfirst = (c == 0 && k == 0) ? 0u : 1u;
-        mma_tf32_ts(hacc, a + 0, h1, ID, hfirst);  // hi_re x [W_re | W_im]_hi
-        mma_tf32_ts(hacc, a + 8, h2, ID, 1u);      // hi_im x [-W_im | W_re]_hi
-        mma_tf32_ts(lacc, a + 0, l1, ID, lfirst);  // hi_re x lo
-        mma_tf32_ts(lacc, a + 8, l2, ID, 1u);      // hi_im x lo
-        mma_tf32_ts(lacc, a + 16, h1, ID, 1u);     // lo_re x hi
-        mma_tf32_ts(lacc, a + 24, h2, ID, 1u);     // lo_im x hi
-        mma_commit(&afree[k]);
+        uint8_t* st = smem + s * SM::RAW_BYTES;
+        mbar_expect_tx(&full[s], SM::RAW_BYTES);
+        tma_load_3d(st, &mapA, &full[s], c * KELEM, m0, b * 2 + 0);
+        tma_load_3d(st + SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * 2 + 1);
+        tma_load_3d(st + 2 * SM::A_TILE, &mapW, &full[s], 2 * c * KELEM, b, blk0);
+        tma_load_3d(st + 2 * SM::A_TILE + SM::W_BOX, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
+        issued = gc + 1;
       }
-      if (ok) mma_commit(&wfree[ps]);
     }
     if (!ok) {
       atomicExch(status, (int)FBST_ERR_TIMEOUT);
       *abort_flag = 1;
+      for (int g = (issued > RS ? issued - RS : 0); g < issued; ++g) (void)mbar_wait(&full[g % RS], (g / RS) & 1);
     }
-    mma_commit(done);
-  } else if (warp >= 4) {
-    // ---------------- converters ----------------
-    const int ct = threadIdx.x - 128;  // A row and tensor-memory lane
-    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t ID = make_idesc(2u, kTileM, 2 * NB, false);
+    int gc = 0, it = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const int s = c % RS, ps = c % PS;
-      if (!mbar_wait(&full[s], (c / RS) & 1)) {
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
+      // The accumulators of the previous tile must have been read out.
+      if (it >= 1 && !mbar_wait(tempty, (it - 1) & 1)) {
         ok = false;
         break;
       }
-      const uint8_t* raw = smem + s * SM::RAW_BYTES;
-      // This thread's row of G for the whole chunk: 16-byte chunk j of row ct sits at j ^ (ct & 7).
-      float4 ar[2 * KSTEPS], ai[2 * KSTEPS];
-#pragma unroll
-      for (int j = 0; j < 2 * KSTEPS; ++j) {
-        const int off = ct * kRowBytes + ((j ^ (ct & 7)) << 4);
-        ar[j] = *reinterpret_cast<const float4*>(raw + off);
-        ai[j] = *reinterpret_cast<const float4*>(raw + SM::A_TILE + off);
-      }
-      if (c >= PS && !mbar_wait(&wfree[ps], ((c / PS) - 1) & 1)) {
-        ok = false;
-        break;
-      }
-      uint8_t* ph = smem + SM::PL_OFF + ps * 2 * SM::WPL;
-      // B: 4 complex values (32 raw bytes) -> one 16-byte chunk (row r, chunk q) of the -W_im, W_re
-      // and W_im rows of both planes, at the swizzled position. The two raw halves are read in an
-      // order that depends on the box, so the 8 threads of one row touch 8 different bank groups.
-#pragma unroll 2
-      for (int j = ct; j < NB * 8; j += 128) {
-        const int r = j >> 3, q = j & 7, box = q >> 2;
-        const uint8_t* rp = raw + 2 * SM::A_TILE + box * SM::W_BOX + r * kRowBytes + (q & 3) * 32;
-        const float4 x0 = *reinterpret_cast<const float4*>(rp + 16 * box);
-        const float4 x1 = *reinterpret_cast<const float4*>(rp + 16 * (1 - box));
-        const float4 a = box ? x1 : x0, bb = box ? x0 : x1;
-        const float4 re = make_float4(a.x, a.z, bb.x, bb.z), im = make_float4(a.y, a.w, bb.y, bb.w);
-        const float4 rh = rna4(re), ih = rna4(im), rl = sub4(re, rh), il = sub4(im, ih);
-        const int off = r * kRowBytes + ((q ^ (r & 7)) << 4);
-        uint8_t* hp = ph + off;
-        uint8_t* lp = ph + SM::WPL + off;
-        *reinterpret_cast<float4*>(hp) = neg4(ih);
-        *reinterpret_cast<float4*>(hp + NB * kRowBytes) = rh;
-        *reinterpret_cast<float4*>(hp + 2 * NB * kRowBytes) = ih;
-        *reinterpret_cast<float4*>(lp) = neg4(il);
-        *reinterpret_cast<float4*>(lp + NB * kRowBytes) = rl;
-        *reinterpret_cast<float4*>(lp + 2 * NB * kRowBytes) = il;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&wconv[ps])) : "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&rawfree[s])) : "memory");
-      // A: split each K step into tensor-memory slot k once the MMAs of the previous chunk freed it.
-#pragma unroll
-      for (int k = 0; k < KSTEPS; ++k) {
-        const float x[2][8] = {{ar[2 * k].x, ar[2 * k].y, ar[2 * k].z, ar[2 * k].w, ar[2 * k + 1].x, ar[2 * k + 1].y,
-                                ar[2 * k + 1].z, ar[2 * k + 1].w},
-                               {ai[2 * k].x, ai[2 * k].y, ai[2 * k].z, ai[2 * k].w, ai[2 * k + 1].x, ai[2 * k + 1].y,
-                                ai[2 * k + 1].z, ai[2 * k + 1].w}};
-        uint32_t hi[16], lo[16];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float h = round_tf32(x[e][i]);
-            hi[e * 8 + i] = __float_as_uint(h);
-            lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
-          }
-        }
-        if (c >= 1 && !mbar_wait(&afree[k], (c - 1) & 1)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+        const int ps = gc % PS;
+        if (!mbar_wait(&wconv[ps], (gc / PS) & 1)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tmem_st16(lane_addr + RING + 32 * k, hi);
-        tmem_st16(lane_addr + RING + 32 * k + 16, lo);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aready[k])) : "memory");
+        const uint32_t bh = smem_u32(smem + SM::PL_OFF + ps * 2 * SM::WPL), bl = bh + SM::WPL;
+        const uint32_t hacc = tmem + ((c & 1) ? H1 : H0), lacc = tmem + LO;
+#pragma unroll
+        for (int k = 0; k < KSTEPS; ++k) {
+          if (!mbar_wait(&aready[k], gc & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a = tmem + RING + 32 * k;  // [hi_re | hi_im | lo_re | lo_im], 8 columns each
+          // rows NB..3NB = [W_re | W_im] and rows 0..2NB = [-W_im | W_re] of the hi and lo planes
+          const uint64_t h1 = smem_desc_sw128(bh + NB * kRowBytes + k * 32), h2 = smem_desc_sw128(bh + k * 32);
+          const uint64_t l1 = smem_desc_sw128(bl + NB * kRowBytes + k * 32), l2 = smem_desc_sw128(bl + k * 32);
+          const uint32_t hfirst = (c < 2 && k == 0) ? 0u : 1u, lfirst = (c == 0 && k == 0) ? 0u : 1u;
+          mma_tf32_ts(hacc, a + 0, h1, ID, hfirst);  // hi_re x [W_re | W_im]_hi
+          mma_tf32_ts(hacc, a + 8, h2, ID, 1u);      // hi_im x [-W_im | W_re]_hi
+          mma_tf32_ts(lacc, a + 0, l1, ID, lfirst);  // hi_re x lo
+          mma_tf32_ts(lacc, a + 8, l2, ID, 1u);      // hi_im x lo
+          mma_tf32_ts(lacc, a + 16, h1, ID, 1u);     // lo_re x hi
+          mma_tf32_ts(lacc, a + 24, h2, ID, 1u);     // lo_im x hi
+          mma_commit(&afree[k]);
+        }
+        if (ok) mma_commit(&wfree[ps]);
+      }
+      if (ok) mma_commit(tfull);
+    }
+    if (!ok) {
+      atomicExch(status, (int)FBST_ERR_TIMEOUT);
+      *abort_flag = 1;
+      // Let the MMAs already issued finish before tensor memory is released.
+      mma_commit(tfull);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 128;  // A row and tensor-memory lane
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    int gc = 0;
+    bool ok = true;
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        const int s = gc % RS, ps = gc % PS;
+        if (!mbar_wait(&full[s], (gc / RS) & 1) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        const uint8_t* raw = smem + s * SM::RAW_BYTES;
+        // This thread's row of G for the whole chunk: 16-byte chunk j of row ct sits at j ^ (ct & 7).
+        float4 ar[2 * KSTEPS], ai[2 * KSTEPS];
+#pragma unroll
+        for (int j = 0; j < 2 * KSTEPS; ++j) {
+          const int off = ct * kRowBytes + ((j ^ (ct & 7)) << 4);
+          ar[j] = *reinterpret_cast<const float4*>(raw + off);
+          ai[j] = *reinterpret_cast<const float4*>(raw + SM::A_TILE + off);
+        }
+        if (gc >= PS && !mbar_wait(&wfree[ps], ((gc / PS) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        uint8_t* ph = smem + SM::PL_OFF + ps * 2 * SM::WPL;
+        // B: 4 complex values (32 raw bytes) -> one 16-byte chunk (row r, chunk q) of the -W_im, W_re
+        // and W_im rows of both planes, at the swizzled position. The two raw halves are read in an
+        // order that depends on the box, so the 8 threads of one row touch 8 different bank groups.
+#pragma unroll 2
+        for (int j = ct; j < NB * 8; j += 128) {
+          const int r = j >> 3, q = j & 7, box = q >> 2;
+          const uint8_t* rp = raw + 2 * SM::A_TILE + box * SM::W_BOX + r * kRowBytes + (q & 3) * 32;
+          const float4 x0 = *reinterpret_cast<const float4*>(rp + 16 * box);
+          const float4 x1 = *reinterpret_cast<const float4*>(rp + 16 * (1 - box));
+          const float4 a = box ? x1 : x0, bb = box ? x0 : x1;
+          const float4 re = make_float4(a.x, a.z, bb.x, bb.z), im = make_float4(a.y, a.w, bb.y, bb.w);
+          const float4 rh = rna4(re), ih = rna4(im), rl = sub4(re, rh), il = sub4(im, ih);
+          const int off = r * kRowBytes + ((q ^ (r & 7)) << 4);
+          uint8_t* hp = ph + off;
+          uint8_t* lp = ph + SM::WPL + off;
+          *reinterpret_cast<float4*>(hp) = neg4(ih);
+          *reinterpret_cast<float4*>(hp + NB * kRowBytes) = rh;
+          *reinterpret_cast<float4*>(hp + 2 * NB * kRowBytes) = ih;
+          *reinterpret_cast<float4*>(lp) = neg4(il);
+          *reinterpret_cast<float4*>(lp + NB * kRowBytes) = rl;
+          *reinterpret_cast<float4*>(lp + 2 * NB * kRowBytes) = il;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&wconv[ps])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&rawfree[s])) : "memory");
+        // A: split each K step into tensor-memory slot k once the MMAs of the previous chunk freed it.
+#pragma unroll
+        for (int k = 0; k < KSTEPS; ++k) {
+          const float x[2][8] = {{ar[2 * k].x, ar[2 * k].y, ar[2 * k].z, ar[2 * k].w, ar[2 * k + 1].x,
+                                  ar[2 * k + 1].y, ar[2 * k + 1].z, ar[2 * k + 1].w},
+                                 {ai[2 * k].x, ai[2 * k].y, ai[2 * k].z, ai[2 * k].w, ai[2 * k + 1].x,
+                                  ai[2 * k + 1].y, ai[2 * k + 1].z, ai[2 * k + 1].w}};
+          uint32_t hi[16], lo[16];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float h = round_tf32(x[e][i]);
+              hi[e * 8 + i] = __float_as_uint(h);
+              lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
+            }
+          }
+          if (gc >= 1 && !mbar_wait(&afree[k], (gc - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          tmem_st16(lane_addr + RING + 32 * k, hi);
+          tmem_st16(lane_addr + RING + 32 * k + 16, lo);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aready[k])) : "memory");
+        }
+        if (!ok) break;
       }
     }
     if (!ok && lane == 0) {
       atomicExch(status, (int)FBST_ERR_TIMEOUT);
       *abort_flag = 1;
     }
-  }
-  __syncwarp();
-
-  // ---------------- Epilogue: warps 0-3 ----------------
-  if (warp < 4) {
-    const bool have = mbar_wait(done, 0);
-    if (!have) {
-      if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
-    } else if (!*abort_flag) {
+  } else if (warp >= 8) {
+    // ---------------- epilogue: accumulators -> bhat ----------------
+    const int ew = warp & 3;  // tensor-memory lane quarter
+    const uint32_t lane_base = tmem + ((uint32_t)(ew * 32) << 16);
+    const bool two = nchunks >= 2;
+    int it = 0;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+      int m0, b, blk0;
+      tile_of(ti, m0, b, blk0);
+      if (!mbar_wait(tfull, it & 1)) {
+        if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int n = m0 + warp * 32 + lane;
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-      const bool two = nchunks >= 2;
+      const int n = m0 + ew * 32 + lane;
 #pragma unroll 1
       for (int j0 = 0; j0 < NB; j0 += 16) {
-        float re[16], im[16], t0[16], t1[16];
-        tmem_ld16(lane_base + H0 + j0, re);
-        tmem_ld16(lane_base + H0 + NB + j0, im);
-        tmem_ld16(lane_base + LO + j0, t0);
-        tmem_ld16(lane_base + LO + NB + j0, t1);
+        uint32_t h0r[16], h0i[16], lor[16], loi[16], h1r[16], h1i[16];
+        tmem_ld16_async(lane_base + H0 + j0, h0r);
+        tmem_ld16_async(lane_base + H0 + NB + j0, h0i);
+        tmem_ld16_async(lane_base + LO + j0, lor);
+        tmem_ld16_async(lane_base + LO + NB + j0, loi);
         if (two) {
-          float u0[16], u1[16];
-          tmem_ld16(lane_base + H1 + j0, u0);
-          tmem_ld16(lane_base + H1 + NB + j0, u1);
+          tmem_ld16_async(lane_base + H1 + j0, h1r);
+          tmem_ld16_async(lane_base + H1 + NB + j0, h1i);
+        }
+        tmem_wait_ld();
+        float re[16], im[16], t0[16], t1[16];
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            re[jj] += u0[jj];
-            im[jj] += u1[jj];
-          }
+        for (int jj = 0; jj < 16; ++jj) {
+          re[jj] = __uint_as_float(h0r[jj]) + (two ? __uint_as_float(h1r[jj]) : 0.f);
+          im[jj] = __uint_as_float(h0i[jj]) + (two ? __uint_as_float(h1i[jj]) : 0.f);
+          t0[jj] = __uint_as_float(lor[jj]);
+          t1[jj] = __uint_as_float(loi[jj]);
+        }
+        if (j0 + 16 >= NB) {
+          // Every accumulator column has been read: the next tile's MMAs may start.
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
         }
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -695,6 +754,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       }
     }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -852,8 +912,11 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   if (r != FBST_OK) return r;
   const int smem = fused_smem<NB>::BYTES;
   FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const dim3 grid((in.N + kTileM - 1) / kTileM, in.B, (nblk + NB - 1) / NB);
-  k_dense_tc_fused<NB><<<grid, 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk, p->d_status);
+  // Persistent: one CTA per SM (shared and tensor memory allow no more), each walking its tiles.
+  const long long ntiles = (long long)((in.N + kTileM - 1) / kTileM) * in.B * ((nblk + NB - 1) / NB);
+  if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
+  const int grid = (int)std::min<long long>(ntiles, sm_count());
+  k_dense_tc_fused<NB><<<grid, 384, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk, p->d_status);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
