@@ -29,8 +29,9 @@ template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V
   return V{a.x * s, a.y * s};
 }
 
-// Largest FFT size of any table or kernel, and the size of the shared twiddle tables
-// (tw[m] = exp(-2*pi*i*m/kTwiddleSize), built in FP64 at plan time).
+// Largest FFT size of any table or kernel, and the size of the shared twiddle tables (the ladder:
+// exp(-2*pi*i*k/M) for k < M/2 at index M/2 - 1 + k, every power of two M <= kMaxFFT, built in
+// FP64 at plan time).
 constexpr int kMaxFFT = 4096;
 constexpr int kTwiddleSize = 4096;
 
@@ -107,7 +108,7 @@ struct fbst_plan_s {
   fbst_band band;
   int device;
 
-  float2* tw32;        // [kTwiddleSize] exp(-2*pi*i*m/kTwiddleSize) rounded to float
+  float2* tw32;        // [kTwiddleSize] twiddle ladder (see kTwiddleSize) rounded to float
   double2* tw64;       // same in double (plan-time FFTs)
 
   // Stage 1a: temporal chirp-z (N snapshots -> L frequencies), S_time output splits.

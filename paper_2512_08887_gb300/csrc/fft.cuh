@@ -5,7 +5,7 @@
 // both the input and the output layout, so pointwise work (chirps, spectra) happens in registers.
 // The transform is a Stockham autosort decimation-in-time FFT: every pass reads radix-R groups
 // at stride P/R straight from registers, applies the twiddles exp(dir*2*pi*i*s*k/(Ns*R)) from an
-// FP64-built table, does a radix-R DFT in registers, and scatters its R outputs to shared memory in
+// FP64-built ladder table (consecutive k at consecutive addresses), does a radix-R DFT in registers, and scatters its R outputs to shared memory in
 // Stockham order; after a barrier each thread reloads its E elements at stride T. R = E except for
 // a final smaller pass when P is not a power of E. The exchange positions are XOR-swizzled per
 // pass (xpos below) so that neither the scatter nor the gather serialises on shared-memory banks.
@@ -133,7 +133,6 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
     constexpr int R = (P / NS < E) ? (P / NS) : E;
     constexpr int T = P / E;
     constexpr int Q = E / R;                       // butterflies per thread in this pass
-    constexpr int TW_STRIDE = kTwiddleSize / (NS * R);
     constexpr int SB = fft_smem_elems<V>(P);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -145,7 +144,7 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
         // of at most three of them (L1 traffic of log2(R) loads instead of R-1).
 #pragma unroll
         for (int s = 1; s < R; s <<= 1) {
-          V ws = tw[s * k * TW_STRIDE];
+          V ws = tw[(NS * R / s) / 2 - 1 + k];  // ladder entry k of M = NS*R/s: exp(-2*pi*i*s*k/(NS*R))
           if constexpr (DIR > 0) ws.y = -ws.y;
           w[s] = ws;
         }

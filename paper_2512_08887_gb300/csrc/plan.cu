@@ -225,11 +225,21 @@ __device__ __forceinline__ bool circ_index(int k, int P, int dmin, int dmax, int
   return false;
 }
 
+// Twiddle ladder: for every power of two M = 2..kTwiddleSize, exp(-2*pi*i*k/M) for k < M/2 at
+// index M/2 - 1 + k (4095 entries; the last slot holds 1). A pass of radix R over sub-transforms
+// of size NS needs exp(-2*pi*i*s*k/(NS*R)) = the ladder entry k of M = NS*R/s for k < NS, so the
+// threads of a warp (consecutive k) read consecutive entries.
 __global__ void k_twiddles(double2* tw64, float2* tw32) {
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < kTwiddleSize; m += gridDim.x * blockDim.x) {
-    const double2 w = expi_pi(-2 * (int64_t)m, kTwiddleSize);  // exp(-2*pi*i*m/4096)
-    tw64[m] = w;
-    tw32[m] = make_float2((float)w.x, (float)w.y);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < kTwiddleSize; idx += gridDim.x * blockDim.x) {
+    double2 w = make_double2(1.0, 0.0);
+    if (idx < kTwiddleSize - 1) {
+      int half = 1;  // M / 2: the largest power of two <= idx + 1
+      while (2 * half <= idx + 1) half *= 2;
+      const int k = idx - (half - 1);
+      w = expi_pi(-2 * (int64_t)k, 2 * half);  // exp(-2*pi*i*k/M), M = 2*half
+    }
+    tw64[idx] = w;
+    tw32[idx] = make_float2((float)w.x, (float)w.y);
   }
 }
 
