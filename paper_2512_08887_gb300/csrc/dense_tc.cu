@@ -21,7 +21,7 @@
 //   thread 32 : MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = NB, K = 32 bytes per step)
 //   warp 1    : tensor-memory allocation / release (2 x NB columns per accumulator, KACC of them)
 //   warps 0-3 : epilogue (tcgen05.ld 32x32b, rows = samples, coalesced complex64 stores)
-// TF32X3 (k_dense_tc_fused, 384 threads) reads plain FP32 planes of G and the stage-1 output w as
+// TF32X3 (k_dense_tc_fused, 384 or 256 threads) reads plain FP32 planes of G and the stage-1 output w as
 // it is (interleaved complex64) and splits both on chip, so no split pass goes through HBM: the
 // split G goes to tensor memory (the MMA's A operand), the split w to shared memory with the real
 // and imaginary parts stacked along N, so each MMA is 128 x 2NB; see the kernel's own comment.
@@ -423,15 +423,17 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 // the accumulation error with L in check.
 // The converters copy a chunk's G rows to registers and release its raw TMA stage before they
 // wait for tensor-memory slots, so the next TMA load is not held up by the MMAs.
-// The kernel is persistent: one CTA per SM walks tiles (beam x 128 samples x up to NB blocks)
-// with stride gridDim.x; the TMA, conversion and tensor-memory rings run on across tiles, and the
-// epilogue warps release the accumulators (tempty) as soon as they have read them, so the next
-// tile's loads and conversions overlap the previous tile's MMAs and stores.
+// PERSIST: one CTA per SM walks tiles (beam x 128 samples x up to NB blocks) with stride
+// gridDim.x; the TMA, conversion and tensor-memory rings run on across tiles, and the epilogue
+// warps release the accumulators (tempty) as soon as they have read them, so the next tile's loads
+// and conversions overlap the previous tile's MMAs and stores. Without PERSIST (256 threads, one
+// tile per CTA, two CTAs per SM) warps 0-3 run the epilogue after the main loop.
 //   thread 0   : TMA producer (raw stage ring, freed by the converters once read)
 //   thread 32  : MMA issuer; warp 1 allocates and frees tensor memory
 //   warps 4-7  : converters (thread = A row = tensor-memory lane)
-//   warps 8-11 : epilogue (tcgen05.ld, FP32 sums, coalesced complex64 stores)
-//   warps 2-3  : idle
+//   warps 8-11 : epilogue (tcgen05.ld, FP32 sums, coalesced complex64 stores; warps 0-3 without
+//                PERSIST)
+//   warps 2-3  : idle until the epilogue
 // ---------------------------------------------------------------------------------------------
 template <int NB>
 struct fused_smem {
@@ -442,7 +444,8 @@ struct fused_smem {
   static constexpr int WPL = 3 * NB * kRowBytes;            // one stacked plane [-W_im | W_re | W_im]
   static constexpr int PL_OFF = RAW_STAGES * RAW_BYTES;     // W planes: PL_STAGES x {hi, lo}
   static constexpr int BAR_OFF = PL_OFF + PL_STAGES * 2 * WPL;
-  static constexpr int BYTES = BAR_OFF + 256 + 1024;        // barriers + alignment slack
+  static constexpr int BAR_BYTES = 512;                     // mbarriers, tensor-memory slot, abort flag
+  static constexpr int BYTES = BAR_OFF + BAR_BYTES + 1024;  // + alignment slack
   static_assert(RAW_BYTES % 1024 == 0 && WPL % 1024 == 0, "1024-byte aligned swizzle atoms");
   static_assert(BYTES <= 227 * 1024, "shared memory");
 };
@@ -472,8 +475,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
       : "memory");
 }
 
-template <int NB>
-__global__ void __launch_bounds__(384, 1)
+template <int NB, bool PERSIST>
+__global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
   using SM = fused_smem<NB>;
@@ -538,6 +541,56 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+
+  // Drain the accumulators of this CTA's tiles into bhat (tensor-memory lane quarter ew).
+  auto epilogue = [&](int ew) {
+    const uint32_t lane_base = tmem + ((uint32_t)(ew * 32) << 16);
+    const bool two = nchunks >= 2;
+    int it = 0;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+      int m0, b, blk0;
+      tile_of(ti, m0, b, blk0);
+      if (!mbar_wait(tfull, it & 1)) {
+        if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int n = m0 + ew * 32 + lane;
+#pragma unroll 1
+      for (int j0 = 0; j0 < NB; j0 += 16) {
+        uint32_t h0r[16], h0i[16], lor[16], loi[16], h1r[16], h1i[16];
+        tmem_ld16_async(lane_base + H0 + j0, h0r);
+        tmem_ld16_async(lane_base + H0 + NB + j0, h0i);
+        tmem_ld16_async(lane_base + LO + j0, lor);
+        tmem_ld16_async(lane_base + LO + NB + j0, loi);
+        if (two) {
+          tmem_ld16_async(lane_base + H1 + j0, h1r);
+          tmem_ld16_async(lane_base + H1 + NB + j0, h1i);
+        }
+        tmem_wait_ld();
+        float re[16], im[16], t0[16], t1[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          re[jj] = __uint_as_float(h0r[jj]) + (two ? __uint_as_float(h1r[jj]) : 0.f);
+          im[jj] = __uint_as_float(h0i[jj]) + (two ? __uint_as_float(h1i[jj]) : 0.f);
+          t0[jj] = __uint_as_float(lor[jj]);
+          t1[jj] = __uint_as_float(loi[jj]);
+        }
+        if (j0 + 16 >= NB) {
+          // Every accumulator column has been read: the next tile's MMAs may start.
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+        }
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int blk = blk0 + j0 + jj;
+          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj] + t0[jj], im[jj] + t1[jj]);
+        }
+      }
+    }
+  };
 
   if (threadIdx.x == 0) {
     // ---------------- TMA producer ----------------
@@ -704,57 +757,14 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       atomicExch(status, (int)FBST_ERR_TIMEOUT);
       *abort_flag = 1;
     }
-  } else if (warp >= 8) {
-    // ---------------- epilogue: accumulators -> bhat ----------------
-    const int ew = warp & 3;  // tensor-memory lane quarter
-    const uint32_t lane_base = tmem + ((uint32_t)(ew * 32) << 16);
-    const bool two = nchunks >= 2;
-    int it = 0;
-    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
-      int m0, b, blk0;
-      tile_of(ti, m0, b, blk0);
-      if (!mbar_wait(tfull, it & 1)) {
-        if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
-        *abort_flag = 1;
-        break;
-      }
-      if (*abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int n = m0 + ew * 32 + lane;
-#pragma unroll 1
-      for (int j0 = 0; j0 < NB; j0 += 16) {
-        uint32_t h0r[16], h0i[16], lor[16], loi[16], h1r[16], h1i[16];
-        tmem_ld16_async(lane_base + H0 + j0, h0r);
-        tmem_ld16_async(lane_base + H0 + NB + j0, h0i);
-        tmem_ld16_async(lane_base + LO + j0, lor);
-        tmem_ld16_async(lane_base + LO + NB + j0, loi);
-        if (two) {
-          tmem_ld16_async(lane_base + H1 + j0, h1r);
-          tmem_ld16_async(lane_base + H1 + NB + j0, h1i);
-        }
-        tmem_wait_ld();
-        float re[16], im[16], t0[16], t1[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          re[jj] = __uint_as_float(h0r[jj]) + (two ? __uint_as_float(h1r[jj]) : 0.f);
-          im[jj] = __uint_as_float(h0i[jj]) + (two ? __uint_as_float(h1i[jj]) : 0.f);
-          t0[jj] = __uint_as_float(lor[jj]);
-          t1[jj] = __uint_as_float(loi[jj]);
-        }
-        if (j0 + 16 >= NB) {
-          // Every accumulator column has been read: the next tile's MMAs may start.
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
-        }
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int blk = blk0 + j0 + jj;
-          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj] + t0[jj], im[jj] + t1[jj]);
-        }
-      }
-    }
+  } else if (PERSIST && warp >= 8) {
+    epilogue(warp & 3);
   }
   __syncwarp();
+  // A single-tile CTA has no epilogue warps: warps 0-3 drain the accumulators after the main loop.
+  if constexpr (!PERSIST) {
+    if (warp < 4) epilogue(warp);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -910,13 +920,18 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   if (r != FBST_OK) return r;
   r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, in.B, nblk, NB);
   if (r != FBST_OK) return r;
+  // NB >= 32: one CTA per SM is all that shared and tensor memory allow, so it is persistent and
+  // walks its tiles. NB = 16: two single-tile CTAs (256 threads, 256 tensor-memory columns) fit
+  // on an SM, which keeps more of G in flight than one persistent CTA does.
+  constexpr bool kPersist = NB >= 32;
   const int smem = fused_smem<NB>::BYTES;
-  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  // Persistent: one CTA per SM (shared and tensor memory allow no more), each walking its tiles.
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB, kPersist>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem));
   const long long ntiles = (long long)((in.N + kTileM - 1) / kTileM) * in.B * ((nblk + NB - 1) / NB);
   if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
-  const int grid = (int)std::min<long long>(ntiles, sm_count());
-  k_dense_tc_fused<NB><<<grid, 384, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk, p->d_status);
+  const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
+  k_dense_tc_fused<NB, kPersist><<<grid, kPersist ? 384 : 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk,
+                                                                           p->d_status);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }

@@ -26,7 +26,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
   long long it0, it1;
   my_range(jl.total, &it0, &it1);
   int j = 0, cur_j = -1, cur_lt = -1;
-  float2 pr[E], ks[E], po[E];
+  float2 pr[E <= 8 ? E : 1], ks[E <= 8 ? E : 1], po[E <= 8 ? E : 1];
   for (long long it = it0; it < it1; ++it) {
     while (j + 1 < jl.n && jl.job[j + 1].first <= it) ++j;
     const space_job& J = jl.job[j];
@@ -36,32 +36,55 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
     const int ell0 = lt * G;
     const int ell = ell0 + g;
     const int ellc = ell < L ? ell : L - 1;
-    if (lt != cur_lt || j != cur_j) {
-      cur_lt = lt;
-      cur_j = j;
+    const float2* row = J.yhat + ((size_t)blk * L + ellc) * M;
+    float2 v[1][E];
+    if constexpr (E <= 8) {
+      // Radix 8: a frequency tile's chirp / spectrum rows stay in registers across the blocks
+      // that share them.
+      if (lt != cur_lt || j != cur_j) {
+        cur_lt = lt;
+        cur_j = j;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int i = t + T * r;
+          pr[r] = i < M ? J.pre[(size_t)ellc * M + i] : make_float2(0.f, 0.f);
+          ks[r] = J.kspec[(size_t)ellc * P + i];
+          po[r] = i < B ? J.post[(size_t)ellc * B + i] : make_float2(0.f, 0.f);
+        }
+      }
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
-        pr[r] = i < M ? J.pre[(size_t)ellc * M + i] : make_float2(0.f, 0.f);
-        ks[r] = J.kspec[(size_t)ellc * P + i];
-        po[r] = i < B ? J.post[(size_t)ellc * B + i] : make_float2(0.f, 0.f);
+        v[0][r] = i < M ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
       }
-    }
-    const float2* row = J.yhat + ((size_t)blk * L + ellc) * M;
-    float2 v[1][E];
+      block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int i = t + T * r;
-      v[0][r] = i < M ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
-    }
-    block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
+      for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], ks[r]);
+      block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], ks[r]);
-    block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
+      for (int r = 0; r < E; ++r) {
+        const int b = t + T * r;
+        if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], po[r]);
+      }
+    } else {
+      // Radix 16 has no registers to spare: the rows are read from L1 where they are used.
+      const float2* pre = J.pre + (size_t)ellc * M;
+      const float2* kspec = J.kspec + (size_t)ellc * P;
+      const float2* post = J.post + (size_t)ellc * B;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int b = t + T * r;
-      if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], po[r]);
+      for (int r = 0; r < E; ++r) {
+        const int i = t + T * r;
+        v[0][r] = i < M ? cmul(row[i], pre[i]) : make_float2(0.f, 0.f);
+      }
+      block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
+#pragma unroll
+      for (int r = 0; r < E; ++r) v[0][r] = cmul(v[0][r], kspec[t + T * r]);
+      block_fft<P, E, 1, +1>(v, fbuf, tw, t, 1 + g);
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const int b = t + T * r;
+        if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], post[b]);
+      }
     }
     __syncthreads();
     float2* out = J.w + (size_t)blk * B * L + ell0;

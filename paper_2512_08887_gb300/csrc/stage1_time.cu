@@ -81,8 +81,8 @@ static int run_time(const job_list<time_job>& jl, int max_Lh, const float2* tw, 
 // Compiled shapes (P, E, G): G*P/E <= 512 threads. The first entry of each P is its default.
 #define FBST_TIME_SHAPES(X)                                                                          \
   X(16, 8, 16) X(32, 8, 16) X(64, 8, 16) X(64, 8, 8) X(128, 8, 8) X(128, 8, 4) X(128, 16, 8)           \
-  X(256, 8, 8) X(256, 8, 4) X(256, 8, 2) X(256, 16, 8) X(256, 16, 4) X(512, 8, 4) X(512, 8, 2)         \
-  X(512, 8, 8) X(512, 16, 4) X(512, 16, 8) X(512, 16, 2) X(1024, 16, 4) X(1024, 8, 4) X(1024, 8, 2)    \
+  X(256, 8, 8) X(256, 8, 4) X(256, 8, 2) X(256, 16, 8) X(256, 16, 4) X(512, 16, 8) X(512, 8, 4)         \
+  X(512, 8, 2) X(512, 8, 8) X(512, 16, 4) X(512, 16, 2) X(1024, 16, 4) X(1024, 8, 4) X(1024, 8, 2)    \
   X(1024, 16, 8) X(1024, 16, 2) X(2048, 16, 4) X(2048, 16, 2) X(2048, 8, 2) X(4096, 16, 2)
 
 int launch_time_jobs(const job_list<time_job>& jl, int P, fft_shape sh, int max_Lh, const float2* tw,
