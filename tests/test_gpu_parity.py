@@ -196,10 +196,14 @@ TC_TOL = {"dense_tf32x3": TOL_E2E, "dense_bf16x3": 1e-3, "dense_tf32": 3e-2}
 
 @pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_bf16x3", "dense_tf32"])
 @pytest.mark.parametrize("case", [("ula", 16, 1, 16, 1, 64, 0.5, 3), ("ula", 13, 1, 10, 1, 24, 0.37, 5),
-                                  ("ura", 8, 8, 8, 8, 64, 0.3, 2), ("ula", 48, 1, 40, 1, 256, 0.5, 70)])
+                                  ("ura", 8, 8, 8, 8, 64, 0.3, 2), ("ula", 48, 1, 40, 1, 256, 0.5, 70),
+                                  ("ula", 40, 1, 160, 1, 200, 0.45, 27)])
 def test_dense_tensor_core_matches_oracle(rng, stage2, case):
-    # Tensor-core dense apply (tcgen05, TMA, TMEM). The last case has 70 blocks: two block groups
-    # and 2N/128 = 4 row tiles; the first ones have N < 128 (row tiles partly outside G_b).
+    # Tensor-core dense apply (tcgen05, TMA, TMEM). The first cases have N < 128 (row tiles partly
+    # outside G_b) and up to 16 blocks (single-tile CTAs for TF32x3). 70 blocks: two block groups of
+    # 64 (persistent TF32x3 CTAs), 2 row tiles. 27 blocks: one partial group of 32, N = 200 (a
+    # partial second row tile), L = 400 (a partial last K chunk of 32) and 320 tiles, more than
+    # the SMs, so persistent CTAs walk several tiles.
     kind, mx, my, bx, by, N, fbw, nblk = case
     plan, pb = make(kind, mx, my, bx, by, N, fbw, stage2=stage2, max_blocks=nblk)
     y = crandn(rng, nblk, pb.M, N)
