@@ -10,7 +10,8 @@ A request is one block of N snapshots of one of the server's arrays (a plan). Th
   block capacity), and admission stops at the first request whose device buffers (input + output)
   would exceed the memory budget, so large requests are not starved;
 * the executor copies the batch's inputs to the device, runs all its arrays in one grouped launch
-  sequence (fbst_batch_enqueue), copies the outputs back and records an event, all on one stream;
+  sequence (fbst_batch_enqueue; a batch of one request runs fbst_execute on the array's resident
+  one-block buffers), copies the outputs back and records an event, all on one stream;
   batches on different streams overlap on the GPU;
 * completions free the requests' memory and their arrays, and admit waiting work.
 
@@ -150,6 +151,9 @@ class GPUExecutor:
         self.dims = [(p.M, p.N, p.B) for p in self.plans]
         self.units = [p.B * p.N for p in self.plans]
         self.out_pool = collections.defaultdict(list)   # pinned host output buffers per array
+        # One-block device buffers per array for single-request batches. The scheduler never has
+        # two batches of the same array in flight, so they are never used twice at once.
+        self.single = {}
 
     def can_submit(self) -> bool:
         return bool(self.free)
@@ -160,10 +164,33 @@ class GPUExecutor:
         M, N, B = self.dims[a]
         return self.torch.empty((1, B, N), dtype=self.torch.complex64).pin_memory()
 
+    def _submit_single(self, r, st):
+        """One request: fbst_execute on the array's resident one-block buffers (no grouping)."""
+        torch = self.torch
+        a = r.array
+        if a not in self.single:
+            M, N, B = self.dims[a]
+            self.single[a] = (torch.empty((1, M, N), dtype=torch.complex64, device="cuda"),
+                              torch.empty((1, B, N), dtype=torch.complex64, device="cuda"))
+        yd, od = self.single[a]
+        yd.copy_(r.y, non_blocking=True)
+        self.plans[a].execute(yd, od, 1, st)
+        h = self._out_buffer(a)
+        h.copy_(od, non_blocking=True)
+        return [], [(r, h)]
+
     def submit(self, batch: list, now: float) -> None:
         torch = self.torch
         si = self.free.pop(0)
         st = self.streams[si]
+        if len(batch) == 1:
+            with torch.cuda.stream(st):
+                keep, hosts = self._submit_single(batch[0], st)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            batch[0].t_launch = now
+            self.inflight.append((si, ev, batch, keep, hosts))
+            return
         groups = collections.defaultdict(list)
         for r in batch:
             groups[r.array].append(r)
