@@ -160,6 +160,10 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
 int fbst_destroy(fbst_plan_t p) {
   if (!p) return FBST_OK;
   cudaDeviceSynchronize();
+  for (cudaStream_t c : {p->copy_in, p->copy_out})
+    if (c) cudaStreamDestroy(c);
+  for (cudaEvent_t e : p->pipe_ev)
+    if (e) cudaEventDestroy(e);
   free_plan_memory(p);
   delete p;
   return FBST_OK;
@@ -251,6 +255,75 @@ int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* strea
   return FBST_OK;
 }
 
+}  // extern "C"
+
+namespace fbst {
+
+// One chunk (at most max_blocks blocks) of fbst_execute_host with the copies overlapped with the
+// kernels: the input moves in up to 4 block parts on the copy_in stream while stage 1 of the
+// previous part runs on s; stage 2 then runs in up to 4 parts, each part's output moving out on
+// the copy_out stream while the next part computes. (Alternating the parts over two streams per
+// direction was measured slower: concurrent copies in one direction contend.) The stage-2 parts are beam ranges for the
+// TF32x3 tensor-core operator (each part of G is read once) and block parts for the
+// Gohberg-Semencul variants; the other dense variants run stage 2 once (a block split would read G
+// once per part). s is left ordered after the outgoing copies.
+static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, int nb, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  cudaEvent_t* ev = p->pipe_ev;
+  const size_t yblk = (size_t)in.M * in.N, hblk = (size_t)in.L * in.M, wblk = (size_t)in.B * in.L,
+               bblk = (size_t)in.B * in.N;
+  const bool gs = in.stage2 == FBST_STAGE2_GS || in.stage2 == FBST_STAGE2_GS_IR1;
+  const bool beam_parts = in.stage2 == FBST_STAGE2_DENSE_TF32X3;
+  // Everything earlier on s (including the previous chunk's reads of stage_y) precedes the copies in.
+  FBST_CUDA_TRY(cudaEventRecord(ev[0], s));
+  FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_in, ev[0], 0));
+  const int q1 = std::min(4, nb);
+  for (int i = 0; i < q1; ++i) {
+    const size_t a = (size_t)nb * i / q1, e = (size_t)nb * (i + 1) / q1;
+    cudaStream_t ci = p->copy_in;
+    FBST_CUDA_TRY(cudaMemcpyAsync(p->stage_y + a * yblk, yh + sizeof(float2) * a * yblk, sizeof(float2) * (e - a) * yblk,
+                                  cudaMemcpyHostToDevice, ci));
+    FBST_CUDA_TRY(cudaEventRecord(ev[1 + i], ci));
+    FBST_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + i], 0));
+    FBST_TRY(launch_czt_time(p, p->stage_y + a * yblk, p->ws_yhat + a * hblk, (int)(e - a), s));
+    FBST_TRY(launch_czt_space(p, p->ws_yhat + a * hblk, p->ws_w + a * wblk, (int)(e - a), s));
+    if (gs) {
+      FBST_TRY(run_stage2(p, p->ws_w + a * wblk, p->stage_bhat + a * bblk, (int)(e - a), s));
+      FBST_CUDA_TRY(cudaEventRecord(ev[5 + i], s));
+      FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev[5 + i], 0));
+      FBST_CUDA_TRY(cudaMemcpyAsync(bh + sizeof(float2) * a * bblk, p->stage_bhat + a * bblk,
+                                    sizeof(float2) * (e - a) * bblk, cudaMemcpyDeviceToHost, p->copy_out));
+    }
+  }
+  if (beam_parts) {
+    const int q2 = std::min(4, in.B);
+    for (int r = 0; r < q2; ++r) {
+      const int b0 = in.B * r / q2, b1 = in.B * (r + 1) / q2;
+      FBST_TRY(launch_stage2_dense_tc_beams(p, p->ws_w, p->stage_bhat, nb, b0, b1 - b0, s));
+      FBST_CUDA_TRY(cudaEventRecord(ev[5 + r], s));
+      FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev[5 + r], 0));
+      // bhat [nb][B][N]: beams [b0, b1) of every block, a strided 2-D copy.
+      const size_t pitch = sizeof(float2) * bblk;
+      FBST_CUDA_TRY(cudaMemcpy2DAsync(bh + sizeof(float2) * (size_t)b0 * in.N, pitch, p->stage_bhat + (size_t)b0 * in.N,
+                                      pitch, sizeof(float2) * (size_t)(b1 - b0) * in.N, nb, cudaMemcpyDeviceToHost,
+                                      p->copy_out));
+    }
+  } else if (!gs) {
+    FBST_TRY(run_stage2(p, p->ws_w, p->stage_bhat, nb, s));
+    FBST_CUDA_TRY(cudaEventRecord(ev[5], s));
+    FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev[5], 0));
+    FBST_CUDA_TRY(cudaMemcpyAsync(bh, p->stage_bhat, sizeof(float2) * (size_t)nb * bblk, cudaMemcpyDeviceToHost,
+                                  p->copy_out));
+  }
+  FBST_CUDA_TRY(cudaEventRecord(ev[9], p->copy_out));
+  FBST_CUDA_TRY(cudaStreamWaitEvent(s, ev[9], 0));
+  return FBST_OK;
+}
+
+}  // namespace fbst
+
+extern "C" {
+
 int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream) {
   if (!p || nblk < 0) return FBST_ERR_INVALID;
   if (nblk == 0) return FBST_OK;
@@ -260,15 +333,14 @@ int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nb
   const int maxb = p->band.max_blocks;
   if (!p->stage_y) FBST_TRY(dmalloc(&p->stage_y, (size_t)maxb * in.M * in.N));
   if (!p->stage_bhat) FBST_TRY(dmalloc(&p->stage_bhat, (size_t)maxb * in.B * in.N));
+  for (cudaStream_t* c : {&p->copy_in, &p->copy_out})
+    if (!*c) FBST_CUDA_TRY(cudaStreamCreateWithFlags(c, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : p->pipe_ev)
+    if (!e) FBST_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
-    const size_t ybytes = sizeof(float2) * (size_t)nb * in.M * in.N;
-    const size_t bbytes = sizeof(float2) * (size_t)nb * in.B * in.N;
-    FBST_CUDA_TRY(cudaMemcpyAsync(p->stage_y, static_cast<const char*>(y_host) + sizeof(float2) * (size_t)c0 * in.M * in.N,
-                                  ybytes, cudaMemcpyHostToDevice, s));
-    FBST_TRY(fbst_execute(p, p->stage_y, p->stage_bhat, nb, stream));
-    FBST_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(bhat_host) + sizeof(float2) * (size_t)c0 * in.B * in.N, p->stage_bhat,
-                                  bbytes, cudaMemcpyDeviceToHost, s));
+    FBST_TRY(execute_host_chunk(p, static_cast<const char*>(y_host) + sizeof(float2) * (size_t)c0 * in.M * in.N,
+                                static_cast<char*>(bhat_host) + sizeof(float2) * (size_t)c0 * in.B * in.N, nb, s));
   }
   FBST_CUDA_TRY(cudaStreamSynchronize(s));
   return FBST_OK;

@@ -144,9 +144,12 @@ struct fbst_plan_s {
   void* ws_tc;         // tensor-core right-hand-side operand (dense TC variants)
   size_t ws_tc_bytes;
 
-  // Host-buffer staging (fbst_execute_host), allocated on first use.
+  // Host-buffer staging (fbst_execute_host), allocated on first use, with the two copy streams
+  // and the events of its pipeline (copies in / out overlapped with the kernels).
   float2* stage_y;     // [max_blocks][M][N]
   float2* stage_bhat;  // [max_blocks][B][N]
+  cudaStream_t copy_in, copy_out;
+  cudaEvent_t pipe_ev[12];
 
   int* d_status;       // device status word (FP64 plan kernels report here)
 
@@ -195,6 +198,9 @@ long long time_items(const time_job& j, fft_shape sh, int P);
 long long space_items(const space_job& j, fft_shape sh, int P);
 int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+// The TF32x3 operator for beams [b0, b0 + nbeam) only (FBST_ERR_UNSUPPORTED for other variants).
+int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
+                                 cudaStream_t s);
 int stage2_launches(const fbst_plan_s* p);
 
 // Plan-time builders (plan.cu / dense_tc.cu).

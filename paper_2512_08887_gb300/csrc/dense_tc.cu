@@ -478,7 +478,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 template <int NB, bool PERSIST>
 __global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
-                 float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
+                 float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int* status) {
   using SM = fused_smem<NB>;
   constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
   constexpr int KELEM = kRowBytes / 4;  // 32 FP32 values of K per chunk
@@ -502,14 +502,15 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (L + KELEM - 1) / KELEM;
-  const int mtiles = (N + kTileM - 1) / kTileM, ntiles = mtiles * B * ((nblk + NB - 1) / NB);
-  // Tile ti: row tile ti % mtiles, beam (ti / mtiles) % B, block group ti / (mtiles B). This CTA
+  const int mtiles = (N + kTileM - 1) / kTileM, ntiles = mtiles * nbeam * ((nblk + NB - 1) / NB);
+  // Tile ti: row tile ti % mtiles, beam b0 + (ti / mtiles) % nbeam, block group ti / (mtiles nbeam)
+  // (beams [b0, b0 + nbeam) of the B beams that G, w and bhat hold). This CTA
   // takes ti = blockIdx.x, blockIdx.x + gridDim.x, ...; every role walks the same sequence, and the
   // chunk counter gc runs on across tiles, so the rings never drain between tiles.
   auto tile_of = [&](int ti, int& m0, int& b, int& blk0) {
     m0 = (ti % mtiles) * kTileM;
-    b = (ti / mtiles) % B;
-    blk0 = (ti / (mtiles * B)) * NB;
+    b = b0 + (ti / mtiles) % nbeam;
+    blk0 = (ti / (mtiles * nbeam)) * NB;
   };
 
   if (threadIdx.x == 0) {
@@ -913,7 +914,8 @@ static int launch_V(const fbst_plan_s* p, const float2* w, float2* bhat, int nbl
 }
 
 template <int NB>
-static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
+                      cudaStream_t s) {
   const fbst_info& in = p->info;
   CUtensorMap mapA, mapW;
   int r = make_map(&mapA, p->Gtc, 4, in.L, in.N, (uint64_t)in.B * 2, kTileM);
@@ -927,26 +929,36 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   const int smem = fused_smem<NB>::BYTES;
   FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB, kPersist>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem));
-  const long long ntiles = (long long)((in.N + kTileM - 1) / kTileM) * in.B * ((nblk + NB - 1) / NB);
+  const long long ntiles = (long long)((in.N + kTileM - 1) / kTileM) * nbeam * ((nblk + NB - 1) / NB);
   if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
   const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
   k_dense_tc_fused<NB, kPersist><<<grid, kPersist ? 384 : 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk,
-                                                                           p->d_status);
+                                                                           b0, nbeam, p->d_status);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
-static int launch_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+static int launch_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
+                        cudaStream_t s) {
   const int want = std::min(round16(nblk), 64);
-  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, s);
-  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, s);
-  return gemm_fused<64>(p, w, bhat, nblk, s);
+  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, b0, nbeam, s);
+  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, b0, nbeam, s);
+  return gemm_fused<64>(p, w, bhat, nblk, b0, nbeam, s);
+}
+
+int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
+                                 cudaStream_t s) {
+  if (variant_of(p->info.stage2) != TC_TF32X3) return FBST_ERR_UNSUPPORTED;
+  if (b0 < 0 || nbeam < 0 || b0 + nbeam > p->info.B) return FBST_ERR_INVALID;
+  if (nblk <= 0 || nbeam == 0) return FBST_OK;
+  if (!p->Gtc) return FBST_ERR_INVALID;
+  return launch_fused(p, w, bhat, nblk, b0, nbeam, s);
 }
 
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
   if (!p->Gtc) return FBST_ERR_INVALID;
-  if (variant_of(p->info.stage2) == TC_TF32X3) return launch_fused(p, w, bhat, nblk, s);
+  if (variant_of(p->info.stage2) == TC_TF32X3) return launch_fused(p, w, bhat, nblk, 0, p->info.B, s);
   if (!p->ws_tc) return FBST_ERR_INVALID;
   switch (variant_of(p->info.stage2)) {
     case TC_BF16X3: return launch_V<TC_BF16X3>(p, w, bhat, nblk, s);

@@ -165,6 +165,23 @@ def test_chunking_host_path_and_determinism(rng):
     assert O.rel_l2(a, O.fbst(pb, y)) < TOL_E2E
 
 
+@pytest.mark.parametrize("stage2", ["gs_ir1", "dense_tf32x3", "dense_fp32"])
+def test_pipelined_host_path_equals_device_path(rng, stage2):
+    # fbst_execute_host overlaps its copies with the kernels: stage 1 and the copies in run in block
+    # parts; stage 2 and the copies out run in block parts (Gohberg-Semencul), in beam ranges with
+    # strided copies (TF32x3) or in one piece (other dense variants). Every part computes exactly
+    # what the device path computes, so the results are bitwise equal. 7 blocks in chunks of 3: the
+    # parts are uneven and the beam count (37) does not split evenly.
+    y = crandn(rng, 7, 40, 96)
+    p, pb = make("ula", 40, 1, 37, 1, 96, 0.45, stage2=stage2, max_blocks=3)
+    a = run(p, "execute", y, (7, 37, 96), 7)
+    host_out = np.full((7, 37, 96), np.nan, dtype=np.complex64)
+    p.execute_host(np.ascontiguousarray(y), host_out, 7)
+    assert p.sync_status() == 0
+    assert np.array_equal(a, host_out)
+    assert O.rel_l2(host_out, O.fbst(pb, y)) < TOL_E2E
+
+
 def test_zero_blocks_is_a_noop_and_bad_args_raise():
     fb = _fb()
     plan, _ = make("ula", 16, 1, 16, 1, 64, 0.5)
