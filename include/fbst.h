@@ -126,9 +126,12 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
  * Blocks are independent contiguous batches of N snapshots (Sec. III-A, streaming paragraph). */
 int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
 
-/* Same as fbst_execute with HOST buffers (pinned or pageable): copies y in, runs, copies bhat out,
- * all on `stream`, and synchronises the stream before returning. Uses plan-owned staging memory
- * (allocated on the first call). */
+/* Same as fbst_execute with HOST buffers (pinned or pageable); synchronises `stream` before
+ * returning, and results are bitwise those of fbst_execute. y is copied in through plan-owned
+ * staging memory (allocated on the first call) in block parts that overlap stage 1. If bhat_host
+ * is pinned (page-locked, mapped) host memory, stage 2 stores into it directly through its device
+ * address; otherwise it is copied out in parts that overlap the rest of stage 2. Two plan-owned
+ * copy streams order themselves after `stream`'s earlier work. */
 int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream);
 
 /* Same result as fbst_execute for callers that cannot allocate device memory at run time (a

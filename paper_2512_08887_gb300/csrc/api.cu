@@ -266,14 +266,18 @@ namespace fbst {
 // direction was measured slower: concurrent copies in one direction contend.) The stage-2 parts are beam ranges for the
 // TF32x3 tensor-core operator (each part of G is read once) and block parts for the
 // Gohberg-Semencul variants; the other dense variants run stage 2 once (a block split would read G
-// once per part). s is left ordered after the outgoing copies.
-static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, int nb, cudaStream_t s) {
+// once per part). With a pinned output, stage 2 runs once and stores into it directly. s is left
+// ordered after the outgoing copies.
+// bh_dev: the device address of bh when the caller's output is pinned (mapped) host memory, else
+// null. Stage 2 then stores straight into it and no output copy is needed.
+static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* bh_dev, int nb, cudaStream_t s) {
   const fbst_info& in = p->info;
   cudaEvent_t* ev = p->pipe_ev;
   const size_t yblk = (size_t)in.M * in.N, hblk = (size_t)in.L * in.M, wblk = (size_t)in.B * in.L,
                bblk = (size_t)in.B * in.N;
-  const bool gs = in.stage2 == FBST_STAGE2_GS || in.stage2 == FBST_STAGE2_GS_IR1;
-  const bool beam_parts = in.stage2 == FBST_STAGE2_DENSE_TF32X3;
+  const bool direct = bh_dev != nullptr;
+  const bool gs = !direct && (in.stage2 == FBST_STAGE2_GS || in.stage2 == FBST_STAGE2_GS_IR1);
+  const bool beam_parts = !direct && in.stage2 == FBST_STAGE2_DENSE_TF32X3;
   // Everything earlier on s (including the previous chunk's reads of stage_y) precedes the copies in.
   FBST_CUDA_TRY(cudaEventRecord(ev[0], s));
   FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_in, ev[0], 0));
@@ -308,6 +312,9 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, int nb, 
                                       pitch, sizeof(float2) * (size_t)(b1 - b0) * in.N, nb, cudaMemcpyDeviceToHost,
                                       p->copy_out));
     }
+  } else if (direct) {
+    FBST_TRY(run_stage2(p, p->ws_w, bh_dev, nb, s));
+    return FBST_OK;
   } else if (!gs) {
     FBST_TRY(run_stage2(p, p->ws_w, p->stage_bhat, nb, s));
     FBST_CUDA_TRY(cudaEventRecord(ev[5], s));
@@ -337,10 +344,19 @@ int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nb
     if (!*c) FBST_CUDA_TRY(cudaStreamCreateWithFlags(c, cudaStreamNonBlocking));
   for (cudaEvent_t& e : p->pipe_ev)
     if (!e) FBST_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // Pinned output: stage 2 writes it in place through its device address (unified addressing).
+  float2* bh_dev = nullptr;
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, bhat_host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+      bh_dev = static_cast<float2*>(at.devicePointer);
+    cudaGetLastError();
+  }
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
     FBST_TRY(execute_host_chunk(p, static_cast<const char*>(y_host) + sizeof(float2) * (size_t)c0 * in.M * in.N,
-                                static_cast<char*>(bhat_host) + sizeof(float2) * (size_t)c0 * in.B * in.N, nb, s));
+                                static_cast<char*>(bhat_host) + sizeof(float2) * (size_t)c0 * in.B * in.N,
+                                bh_dev ? bh_dev + (size_t)c0 * in.B * in.N : nullptr, nb, s));
   }
   FBST_CUDA_TRY(cudaStreamSynchronize(s));
   return FBST_OK;
