@@ -78,7 +78,7 @@ const char* fbst_status_string(int status) {
     case FBST_ERR_INVALID: return "FBST_ERR_INVALID: a size, pointer or parameter is out of range";
     case FBST_ERR_OOM: return "FBST_ERR_OOM: allocation failed";
     case FBST_ERR_CUDA: return "FBST_ERR_CUDA: a CUDA call failed";
-    case FBST_ERR_UNSUPPORTED: return "FBST_ERR_UNSUPPORTED: valid but not supported by this build";
+    case FBST_ERR_UNSUPPORTED: return "FBST_ERR_UNSUPPORTED: valid but not supported by this library";
     case FBST_ERR_TIMEOUT: return "FBST_ERR_TIMEOUT: a bounded device wait gave up";
     case FBST_ERR_NUMERIC: return "FBST_ERR_NUMERIC: a Toeplitz system is not numerically positive definite";
     default: return "unknown fbst status";
