@@ -60,8 +60,10 @@ def run(plan, fn, x, out_shape, nblk):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,N", [(16, 64), (13, 24), (256, 256), (40, 512)])
+@pytest.mark.parametrize("M,N", [(16, 64), (13, 24), (256, 256), (40, 512), (8, 1024)])
 def test_czt_time_matches_oracle(rng, M, N):
+    # (8, 1024): L = 2048 outputs (P = 2048), the largest block a plan accepts (its
+    # Gohberg-Semencul circulants then have the largest size, 2L = 4096).
     plan, pb = make("ula", M, 1, M, 1, N, 0.5)
     y = crandn(rng, 3, M, N)
     got = run(plan, "czt_time", y, (3, pb.L, M), 3)
@@ -72,8 +74,10 @@ def test_czt_time_matches_oracle(rng, M, N):
 @pytest.mark.parametrize("case", [
     ("ula", 16, 1, 16, 1, 64, 0.5), ("ula", 13, 1, 10, 1, 24, 0.37), ("ula", 256, 1, 256, 1, 256, 0.5),
     ("ula", 100, 1, 150, 1, 64, 0.8), ("ura", 4, 4, 4, 4, 32, 0.3), ("ura", 8, 8, 8, 8, 64, 0.3),
+    ("ula", 1024, 1, 1024, 1, 32, 0.5), ("ula", 2048, 1, 2048, 1, 16, 0.5),
 ])
 def test_czt_matches_oracle(rng, case):
+    # The last two: spatial transforms of P = 2048 and P = 4096 (the largest).
     kind, mx, my, bx, by, N, fbw = case
     plan, pb = make(kind, mx, my, bx, by, N, fbw)
     y = crandn(rng, 2, pb.M, N)
@@ -96,8 +100,9 @@ def test_levinson_generators_match_dense_solve(case):
 @pytest.mark.parametrize("stage2", ["gs_ir1", "dense_fp32", "gs"])
 @pytest.mark.parametrize("case", [("ula", 16, 1, 16, 1, 64, 0.5), ("ula", 13, 1, 10, 1, 24, 0.37),
                                   ("ura", 8, 8, 8, 8, 64, 0.3), ("ula", 64, 1, 64, 1, 512, 0.5),
-                                  ("ula", 1, 1, 1, 1, 16, 0.5)])
+                                  ("ula", 1, 1, 1, 1, 16, 0.5), ("ula", 4, 1, 4, 1, 1024, 0.5)])
 def test_toeplitz_apply_matches_oracle(rng, stage2, case):
+    # The last case has L = 2048: Gohberg-Semencul circulants of P = 4096 (the largest).
     # White-noise input puts energy where A_b is smallest (the worst case for FP32). Plain GS in
     # FP32 loses about eps32 * cond(A_b) ~ 6e-8 * 2/delta_rel to the difference of its two
     # triangular products, so it is held to 2e-4; the refined and dense variants to 1e-5.
