@@ -170,9 +170,16 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
   const int mx = axx.Ma, bx = axx.Ba, my = axy.Ma, by = axy.Ba;
   const int M = mx * my, B = bx * by;
   const int g = threadIdx.x / T, t = threadIdx.x % T;
+  static_assert(TL == 4, "the tile swizzle permutes the 4 frequencies of a slot");
   float2* fbuf = sm + g * SB;
-  float2* Z = sm + G * SB;      // [mx][by]
-  float2* tile = Z + mx * by;   // [B][TL]
+  // Z [mx][zs] and the output tile [bx][ts] are swizzled so that neither the row-wise nor the
+  // column-wise accesses of a half-warp (two transform groups of 8) share a bank: Z column c of
+  // row kx sits at c ^ (kx & 7) with rows round8(by) + 8 apart; the frequency j of output
+  // (a, c) sits at c*TL + (j ^ (a & 3)) with rows by*TL + 2 apart. Both only permute within
+  // aligned groups, so every index stays inside its row.
+  const int zs = ((by + 7) & ~7) + 8, ts = by * TL + 2;
+  float2* Z = sm + G * SB;
+  float2* tile = Z + mx * zs;
   const int ntile = (L + TL - 1) / TL;
   long long it0, it1;
   my_range((long long)ntile * nblk, &it0, &it1);
@@ -198,7 +205,7 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int c = t + T * r;
-          if (act && c < by) Z[kx * by + c] = cmul(v[0][r], axy.post[(size_t)ell * by + c]);
+          if (act && c < by) Z[kx * zs + (c ^ (kx & 7))] = cmul(v[0][r], axy.post[(size_t)ell * by + c]);
         }
       }
       __syncthreads();
@@ -209,7 +216,8 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int kx = t + T * r;
-          v[0][r] = (act && kx < mx) ? cmul(Z[kx * by + c], axx.pre[(size_t)ell * mx + kx]) : make_float2(0.f, 0.f);
+          v[0][r] = (act && kx < mx) ? cmul(Z[kx * zs + (c ^ (kx & 7))], axx.pre[(size_t)ell * mx + kx])
+                                     : make_float2(0.f, 0.f);
         }
         block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
@@ -218,15 +226,15 @@ k_czt_space_ura(const float2* __restrict__ yhat, float2* __restrict__ w, fbst_ax
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int a = t + T * r;
-          if (act && a < bx) tile[(a * by + c) * TL + j] = cmul(v[0][r], axx.post[(size_t)ell * bx + a]);
+          if (act && a < bx) tile[a * ts + c * TL + (j ^ (a & 3))] = cmul(v[0][r], axx.post[(size_t)ell * bx + a]);
         }
       }
       __syncthreads();
     }
     float2* out = w + (size_t)blk * B * L + ell0;
     for (int idx = threadIdx.x; idx < B * TL; idx += blockDim.x) {
-      const int b = idx / TL, jj = idx % TL;
-      if (ell0 + jj < L) out[(size_t)b * L + jj] = tile[idx];
+      const int b = idx / TL, jj = idx % TL, a = b / by, c = b % by;
+      if (ell0 + jj < L) out[(size_t)b * L + jj] = tile[a * ts + c * TL + (jj ^ (a & 3))];
     }
     __syncthreads();
   }
@@ -242,8 +250,9 @@ static int czt_space_ura_P(const fbst_plan_s* p, const float2* yhat, float2* w, 
   const fbst_info& in = p->info;
   const fbst_axis_tables& axx = p->ax[0];
   const fbst_axis_tables& axy = p->same_axes ? p->ax[0] : p->ax[1];
-  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)axx.Ma * axy.Ba +
-                                        (size_t)in.B * TL);
+  const size_t zs = ((size_t)axy.Ba + 7) / 8 * 8 + 8, ts = (size_t)axy.Ba * TL + 2;  // as in the kernel
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)axx.Ma * zs +
+                                        (size_t)axx.Ba * ts);
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
   FBST_TRY(allow_max_smem(k_czt_space_ura<P, TL, NTH>));
   const long long items = (long long)((in.L + TL - 1) / TL) * nblk;
