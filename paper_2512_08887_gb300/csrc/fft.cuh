@@ -128,7 +128,8 @@ __device__ __forceinline__ void dft(V* x) {
 // One Stockham pass (current sub-transform size NS) followed by the remaining passes.
 // v[f][r] is element t + T*r of transform f; sbuf holds NF consecutive buffers of P elements.
 template <int P, int E, int NF, int DIR, int NS, typename V>
-__device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t, int bar) {
+__device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __restrict__ tw, int t, int bar,
+                                           int gkey) {
   if constexpr (NS < P) {
     constexpr int R = (P / NS < E) ? (P / NS) : E;
     constexpr int T = P / E;
@@ -173,7 +174,7 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
           for (int s = 0; s < R; ++s) v[f][q + Q * s] = x[s];
         } else {
 #pragma unroll
-          for (int s = 0; s < R; ++s) sbuf[f * SB + xpos<P, NS, R>(base + s * NS)] = x[s];
+          for (int s = 0; s < R; ++s) sbuf[f * SB + (xpos<P, NS, R>(base + s * NS) ^ gkey)] = x[s];
         }
       }
     }
@@ -184,10 +185,10 @@ __device__ __forceinline__ void fft_passes(V (&v)[NF][E], V* sbuf, const V* __re
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
 #pragma unroll
-        for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + xpos<P, NS, R>(t + T * r)];
+        for (int r = 0; r < E; ++r) v[f][r] = sbuf[f * SB + (xpos<P, NS, R>(t + T * r) ^ gkey)];
       }
       fft_sync<T>(bar);
-      fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t, bar);
+      fft_passes<P, E, NF, DIR, NS * R>(v, sbuf, tw, t, bar, gkey);
     }
   }
 }
@@ -200,7 +201,14 @@ __device__ __forceinline__ void block_fft(V (&v)[NF][E], V* sbuf, const V* __res
   static_assert((P & (P - 1)) == 0 && P >= 2 && P <= kMaxFFT, "P must be a power of two <= 4096");
   static_assert(E >= 2 && E <= 16 && (E & (E - 1)) == 0 && E <= P, "E must be a power of two <= 16");
   static_assert(P / E <= 32 || (P / E) % 32 == 0, "a group barrier spans whole warps");
-  fft_passes<P, E, NF, DIR, 1>(v, sbuf, tw, t, bar);
+  // Groups of fewer than 16 threads share a half-warp with their neighbours, whose buffers start on
+  // the same bank: the low 4 bits of group g's exchange positions are XORed with (g * 13) & 15
+  // (g * 9 for 2-thread groups), which keeps the scatter and gather of neighbouring groups apart
+  // (checked for every radix schedule with 2, 4 and 8 threads per group). The XOR permutes each
+  // aligned run of 16 positions, so it stays inside a buffer of P >= 16.
+  constexpr int T = P / E;
+  const int gkey = (bar > 0 && T >= 2 && T < 16 && P >= 16) ? (((bar - 1) * (T == 2 ? 9 : 13)) & 15) : 0;
+  fft_passes<P, E, NF, DIR, 1>(v, sbuf, tw, t, bar, gkey);
 }
 
 }  // namespace fbst
