@@ -1,0 +1,55 @@
+"""The benchmark's roofline arithmetic (host logic, no GPU): algorithmic bytes and FLOPs per launch,
+the choice of the binding roof, and the FP32 ALU peak derived from unit counts and clocks."""
+import importlib.util
+import os
+from types import SimpleNamespace
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+# The 256-element ULA case: M = B = N = 256, L = 512, 64 blocks; stage 2 = 6 (TF32x3 tensor cores).
+C2 = SimpleNamespace(M=256, N=256, B=256, L=512, S_time=2, P_time=512, P_space_x=512, P_gs=1024,
+                     P_rec=512, S_rec=2, stage2=6)
+PEAKS = {"hbm_gbs": 6690.8, "bf16_tflops": 1972.2, "sm_max_mhz": 2070.0}
+
+
+def test_tf32x3_stage2_bytes_flops_and_bound():
+    b = _bench()
+    # Compulsory bytes of one 64-block launch: G as FP32 re/im planes, w read once, bhat written.
+    g_bytes = 256 * 2 * 256 * 512 * 4
+    w_bytes = 256 * 512 * 64 * 8
+    out_bytes = 256 * 256 * 64 * 8
+    assert (g_bytes, w_bytes, out_bytes) == (268435456, 67108864, 33554432)
+    # 8 N L flops per beam-block (complex multiply-add), 3 split-TF32 products per complex term.
+    assert b.flop_model(C2)["stage2"] * 64 == 8 * 256 * 512 * 256 * 64
+    # At the measured peaks HBM binds: 369.1 MB / 6690.8 GB/s = 55.2 us against
+    # 3 x 17.18 GFLOP / (0.5 x 1972.2 TFLOP/s) = 52.3 us of tensor work.
+    r = b.roofline("stage2", C2, 64, 0.1, PEAKS, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6690.8
+    assert r["achieved"] == pytest.approx((g_bytes + w_bytes + out_bytes) / 1e-4 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6690.8)
+    # With a much slower memory the same launch is tensor-bound, against the TF32 peak (bf16 / 2).
+    r = b.roofline("stage2", C2, 64, 0.1, dict(PEAKS, hbm_gbs=20000.0), "measured")
+    assert r["bound"] == "tensor" and r["peak"] == pytest.approx(986.1)
+    assert r["achieved"] == pytest.approx(3 * 8 * 256 * 512 * 256 * 64 / 1e-4 / 1e12)
+
+
+def test_fft_kernels_are_reported_against_the_fp32_alu_peak():
+    b = _bench()
+    r = b.roofline("czt_time", C2, 64, 0.0765, PEAKS, "measured")
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz.
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    # One forward and S = 2 inverse transforms of 512 points per sensor-block, 5 P log2 P each,
+    # plus the chirp and spectrum multiplies (6 flops per complex multiply).
+    per_sensor = 3 * 5 * 512 * 9 + 6 * (256 + 2 * 512 + 512)
+    assert b.flop_model(C2)["czt_time"] == per_sensor * 256
+    assert r["achieved"] == pytest.approx(per_sensor * 256 * 64 / 0.0765e-3 / 1e12)
