@@ -109,7 +109,9 @@ typedef struct {
   size_t workspace_bytes; /* device bytes of the plan's per-call workspace */
 } fbst_info;
 
-/* Host-only: derive the plan parameters without touching a GPU. Same validation as fbst_plan.
+/* Host-only: derive the plan parameters of Sec. III-A and Sec. VI (the basis size L = gamma*N and
+ * frequency grid of Eq. (3), delta of Eq. (5), the bounds of Eq. (4) and Eq. (8)) and the transform
+ * sizes of Sec. IV and Sec. V, without touching a GPU. Same validation as fbst_plan.
  * M and B must equal mx*my and bx*by. Returns FBST_ERR_INVALID / FBST_ERR_UNSUPPORTED on bad
  * input and fills *out otherwise. */
 int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fbst_band* band, fbst_info* out);
@@ -126,15 +128,19 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
  * Blocks are independent contiguous batches of N snapshots (Sec. III-A, streaming paragraph). */
 int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
 
-/* Same as fbst_execute with HOST buffers (pinned or pageable); synchronises `stream` before
+/* The transform of Sec. III-A (as fbst_execute) with HOST buffers (pinned or pageable); the host
+ * copies have no counterpart in the paper. Synchronises `stream` before
  * returning, and results are bitwise those of fbst_execute. y is copied in through plan-owned
  * staging memory (allocated on the first call) in block parts that overlap stage 1. If bhat_host
  * is pinned (page-locked, mapped) host memory, stage 2 stores into it directly through its device
  * address; otherwise it is copied out in parts that overlap the rest of stage 2. Two plan-owned
- * copy streams order themselves after `stream`'s earlier work. */
+ * copy streams order themselves after `stream`'s earlier work. Errors as fbst_execute, plus
+ * FBST_ERR_OOM when the staging allocation fails and FBST_ERR_CUDA when a copy fails
+ * (fbst_last_error says why). */
 int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream);
 
-/* Same result as fbst_execute for callers that cannot allocate device memory at run time (a
+/* The transform of Sec. III-A, same result as fbst_execute, for callers that cannot allocate
+ * device memory at run time (a
  * real-time loop that must not block in the allocator, a fixed start-up memory budget, code
  * running under stream capture). The paper has no counterpart; this is a library convenience.
  * The intermediates live in one 64 MiB static device array of the library instead of the plan's
@@ -162,29 +168,35 @@ int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* str
  * bhat_b = F_u (F_b^H F_b + delta I)^{-1} w_b, with the plan's stage-2 variant. */
 int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream);
 
-/* Synchronise `stream`, then return and clear the plan's device status word: FBST_OK, or the
+/* Error reporting; no counterpart in the paper. Synchronise `stream`, then return and clear the
+ * plan's device status word: FBST_OK, or the
  * error a kernel recorded since the last check (FBST_ERR_TIMEOUT when a bounded device-side wait
  * of the tensor-core kernel gave up; its outputs are then not valid). */
 int fbst_sync_status(fbst_plan_t p, void* stream);
 
-/* Copy the derived parameters of a plan. */
+/* Copy the derived parameters of a plan (those fbst_derive returns: Sec. III-A, Sec. IV-VI) to the
+ * caller's *out. FBST_ERR_INVALID if p or out is NULL. */
 int fbst_plan_info(fbst_plan_t p, fbst_info* out);
 
 /* Copy the first column x_b of A_b^{-1} for every beam (FP64 Levinson result, Sec. V) to host
  * memory `x_host` as [B][L] complex128 (interleaved doubles). Exposed for testing. */
 int fbst_plan_generators(fbst_plan_t p, void* x_host);
 
-/* Free the plan and all of its device memory. Waits for the plan's outstanding work. NULL is OK. */
+/* Resource management; no counterpart in the paper. Free the plan and all of its device memory.
+ * Waits for the plan's outstanding work. NULL is OK. */
 int fbst_destroy(fbst_plan_t p);
 
-/* Static human-readable name of a status code. */
+/* Error reporting; no counterpart in the paper. Static human-readable name of a status code (the
+ * library owns the string; an unknown code gives "unknown fbst status"). */
 const char* fbst_status_string(int status);
 
-/* Description of the last CUDA failure seen by this host thread ("" if none). The string is owned
+/* Error reporting; no counterpart in the paper. Description of the last CUDA failure seen by
+ * this host thread ("" if none). The string is owned
  * by the library and stays valid until the next failing call on the same thread. */
 const char* fbst_last_error(void);
 
-/* Number of kernels one fbst_execute of nblk blocks launches (for launch accounting). */
+/* Launch accounting; no counterpart in the paper. Number of kernels one fbst_execute of nblk
+ * blocks launches (stage 1 of Sec. IV plus stage 2 of Sec. V); 0 for a NULL plan or nblk <= 0. */
 int fbst_launch_count(fbst_plan_t p, int nblk);
 
 /* ---------------------------------------------------------------------------------------------
@@ -197,7 +209,9 @@ int fbst_launch_count(fbst_plan_t p, int nblk);
 typedef struct fbst_batch_s* fbst_batch_t;
 
 /* Group `count` distinct plans into a batch (the batch keeps pointers; the plans must outlive
- * it and must not run elsewhere while a batch run using them is in flight). */
+ * it and must not run elsewhere while a batch run using them is in flight). The grouping has no
+ * counterpart in the paper; each plan still computes the transform of Sec. III-A. FBST_ERR_INVALID
+ * for count < 1, a NULL or repeated plan. */
 int fbst_batch_create(fbst_batch_t* out, const fbst_plan_t* plans, int count);
 
 /* Run plan i on nblk[i] blocks (0 <= nblk[i] <= that plan's max_blocks): y[i] ([nblk][M][N]) ->
@@ -210,27 +224,31 @@ int fbst_batch_execute(fbst_batch_t b, const void* const* y, void* const* bhat, 
  * callers whose pointer sets change on every call, such as a continuous-batching server). */
 int fbst_batch_enqueue(fbst_batch_t b, const void* const* y, void* const* bhat, const int* nblk, void* stream);
 
-/* Kernels in one graph replay of the batch (0 before the first run). */
+/* Launch accounting; no counterpart in the paper. Kernels in one graph replay of the batch (0
+ * before the first run). */
 int fbst_batch_launch_count(fbst_batch_t b);
 
-/* Release the batch (not its plans). */
+/* Resource management; no counterpart in the paper. Release the batch and its captured graph
+ * (not its plans). NULL is OK. */
 int fbst_batch_destroy(fbst_batch_t b);
 
 /* ---------------------------------------------------------------------------------------------
  * Launch shapes of the two stage-1 kernels: the Stockham radix (elements per thread, E) and the
  * transforms per CTA (G). Not part of the method; performance only, results stay within rounding.
  * ------------------------------------------------------------------------------------------- */
-/* Time every compiled shape of the temporal and the spatial chirp-z kernels for this plan on
+/* Time every compiled shape of the temporal and the spatial chirp-z kernels of Sec. IV for this
+ * plan on
  * nblk blocks (on the plan's workspace and a temporary input buffer it allocates), keep the
  * fastest in the plan, and write {time_E, time_G, space_E, space_G} to shapes4 (may be NULL).
  * Synchronises `stream`. Not allowed during stream capture. */
 int fbst_autotune(fbst_plan_t p, int nblk, void* stream, int* shapes4);
 
-/* Set the shapes explicitly ({0, 0} restores the built-in default for that kernel);
+/* Set the shapes of the Sec. IV kernels explicitly ({0, 0} restores the built-in default for
+ * that kernel);
  * FBST_ERR_UNSUPPORTED if no kernel of that shape is compiled for the plan's transform size. */
 int fbst_set_shapes(fbst_plan_t p, int time_E, int time_G, int space_E, int space_G);
 
-/* Read the shapes in use: {time_E, time_G, space_E, space_G}. */
+/* Read the shapes of the Sec. IV kernels in use into shapes4: {time_E, time_G, space_E, space_G}. */
 int fbst_get_shapes(fbst_plan_t p, int* shapes4);
 
 #ifdef __cplusplus
