@@ -233,6 +233,65 @@ def dense_operator(pb: Problem, b: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------------
+# Beamspace interference nulling (Sec. VI-B, Eq. (14))
+# ----------------------------------------------------------------------------------------------
+
+def cross_gram(pb: Problem, b: int, p: int) -> np.ndarray:
+    """F_b^H F_p (L x L) for beams b and p by direct sums: the product inside G_p of Eq. (14).
+
+    As in gram(), [F_b]_{(m,n),ell} = c_{b,m} * E[n,ell] * phi_b[ell,m] with the carrier
+    c_{b,m} = exp(-2j*pi*tau_{b,m}/fb), so
+    [F_b^H F_p]_{ell,k} = (sum_n conj(E[n,ell]) E[n,k]) * (sum_m conj(c_{b,m} phi_b[ell,m]) c_{p,m} phi_p[k,m]).
+    For b != p the carriers no longer cancel and the element sum is not a function of k - ell.
+    """
+    E = F_u(pb)                                                                   # (N, L)
+    tb, tp = pb.tau([b])[0], pb.tau([p])[0]                                       # (M,)
+    el = lambda tau: (np.exp(-TWO_PI_J * tau / pb.frac_bw)[None, :]
+                      * np.exp(-TWO_PI_J * pb.epsilon * np.multiply.outer(pb.lprime, tau) / pb.L))  # (L, M)
+    return (E.conj().T @ E) * (el(tb).conj() @ el(tp).T)
+
+
+class NullingFactors:
+    """Per-plan part of Eq. (14): the stage-2 factors of the output beams and of the interferer
+    beams, and the cross Gram matrices F_b^H F_p of every (output beam, interferer) pair."""
+
+    def __init__(self, pb: Problem, interferers, beams=None):
+        self.pb = pb
+        self.interferers = [int(p) for p in interferers]
+        self.out = Stage2Factors(pb, beams)
+        self.intf = Stage2Factors(pb, self.interferers)
+        self.C = [[cross_gram(pb, int(b), p) for p in self.interferers] for b in self.out.beams]
+
+    def coefficients(self, w: np.ndarray, w_int: np.ndarray) -> np.ndarray:
+        """The bracket of Eq. (14), w_b - sum_p F_b^H F_p (F_p^H F_p + delta I)^{-1} w_p.
+
+        w: (nblk, nbeams, L) for the output beams, w_int: (nblk, P, L) for the interferer beams.
+        """
+        w = np.asarray(w, dtype=np.complex128)
+        out = w.copy()
+        if self.interferers:
+            beta_int = self.intf.coefficients(w_int)                     # (nblk, P, L)
+            for i in range(len(self.out.beams)):
+                for j in range(len(self.interferers)):
+                    out[:, i, :] -= beta_int[:, j, :] @ self.C[i][j].T
+        return out
+
+
+def fbst_nulled(pb: Problem, y: np.ndarray, interferers, beams=None,
+                factors: NullingFactors | None = None) -> np.ndarray:
+    """FBST with beamspace nulling of the interferer beams (Eq. (14)): y (nblk, M, N) -> bhat
+    (nblk, nbeams, N) with bhat_b = F_u A_b^{-1} (w_b - sum_p F_b^H F_p A_p^{-1} w_p)."""
+    y = np.asarray(y)
+    if y.ndim == 2:
+        y = y[None]
+    if factors is None:
+        factors = NullingFactors(pb, interferers, beams)
+    w = fan_coefficients(pb, y, factors.out.beams)
+    w_int = fan_coefficients(pb, y, factors.interferers) if factors.interferers else None
+    return factors.out.apply(factors.coefficients(w, w_int))
+
+
+# ----------------------------------------------------------------------------------------------
 # Tools used by the pins (not part of the method)
 # ----------------------------------------------------------------------------------------------
 

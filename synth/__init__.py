@@ -14,4 +14,5 @@ from .planewave import (  # noqa: F401
     ula_config,
     ura_config,
     uneven_ula_instances,
+    interference_config,
 )

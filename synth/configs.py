@@ -7,11 +7,14 @@ C3  32x32 rectangular array (M=1024), N=512, 32x32 beam grid (B=1024), fb=0.3; K
     from the unit disk, 10 dB; nblk blocks of one record; seed 1003.
 C4  64 independent linear arrays, M = 2^U{5..10}, N from {128,256,512,1024}, B=M, fb ~ U[0.2,0.6]
     rounded to 1e-3, K=4 plane waves, 15 dB, one block each, per-instance child seeds of 1004.
+C2N the C2 array and grid with one unit-power source on grid beam 160 and two interferers on grid
+    beams 64 and 96 at 20 dB above it, 10 dB SNR, 64 blocks; seed 1005. Workload of the beamspace
+    interference nulling (Sec. VI-B), which removes beams 64 and 96.
 Every waveform is a sum of Q sinusoids with CN(0, 1/Q) weights and uniform in-band frequencies.
 """
 from __future__ import annotations
 
-from .planewave import ula_config, ura_config, uneven_ula_instances
+from .planewave import interference_config, ula_config, ura_config, uneven_ula_instances
 
 CONFIGS = {
     "C1": dict(kind="ula", mx=16, my=1, bx=16, by=1, N=64, frac_bw=0.5, K=3, snr_db=20.0, seed=1001, nblk=1),
@@ -29,6 +32,26 @@ def config_data(name: str, nblk: int | None = None, Q: int = 256) -> dict:
         d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
     else:
         d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
+    d.update(c)
+    return d
+
+
+NULLING = {
+    "C2N": dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, source_beams=[160],
+                interferers=[64, 96], inr_db=20.0, snr_db=10.0, seed=1005, nblk=64),
+}
+
+
+def nulling_data(name: str, nblk: int | None = None, Q: int = 256) -> dict:
+    """Seeded data of a nulling workload. Grid beam b of a linear array looks at u = -1 + 2b/B, so
+    the sources and interferers sit exactly on grid beams."""
+    c = dict(NULLING[name])
+    if nblk is not None:
+        c["nblk"] = nblk
+    grid = lambda b: (-1.0 + 2.0 * b / c["bx"], 0.0)
+    d = interference_config(c["kind"], c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"],
+                            [grid(b) for b in c["source_beams"]], [grid(b) for b in c["interferers"]],
+                            c["inr_db"], c["snr_db"], c["seed"], Q=Q)
     d.update(c)
     return d
 

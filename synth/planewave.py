@@ -155,6 +155,23 @@ def ura_config(mx: int, my: int, N: int, nblk: int, frac_bw: float, K: int, snr_
             "y": _blocks(rec, N, nblk)}
 
 
+def interference_config(kind: str, mx: int, my: int, N: int, nblk: int, frac_bw: float,
+                        source_dirs, interferer_dirs, inr_db: float, snr_db: float | None,
+                        seed: int, Q: int = 256) -> dict:
+    """Unit-power sources at source_dirs and interferers of power 10^(inr_db/10) at
+    interferer_dirs (lists of direction cosines (u, v)), one record cut into nblk blocks."""
+    ss = np.random.SeedSequence(seed)
+    rs, rn = (np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(2))
+    geom = ArrayGeometry(kind, mx, my)
+    src = []
+    for (u, v), power in [(d, 1.0) for d in source_dirs] + [(d, 10.0 ** (inr_db / 10.0)) for d in interferer_dirs]:
+        amp = (rs.standard_normal(Q) + 1j * rs.standard_normal(Q)) * np.sqrt(0.5 * power / Q)
+        src.append(Source(float(u), float(v), amp, rs.uniform(-0.5, 0.5, Q)))
+    rec = array_record(geom, src, frac_bw, nblk * N, snr_db, rn)
+    return {"geom": geom, "sources": src, "frac_bw": frac_bw, "N": N, "nblk": nblk,
+            "y": _blocks(rec, N, nblk)}
+
+
 def uneven_ula_instances(seed: int, count: int = 64, K: int = 4, snr_db: float = 15.0,
                          m_exponents=(5, 10), n_choices=(128, 256, 512, 1024),
                          fb_range=(0.2, 0.6), Q: int = 64, with_data: bool = True) -> list[dict]:
