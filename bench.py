@@ -8,7 +8,7 @@ FP64 oracle, reported on every run); --stage2 gs_ir1 selects the Gohberg-Semencu
 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload C2|C3|ULA1024|C4|C5]
+                  [--workload C2|C3|ULA1024|C4|C5|C2N] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own 64 blocks (weak
 scaling; the method has no cross-block exchange, so there is no collective on the data path).
@@ -308,6 +308,172 @@ def run_c5(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def null_roofline(B: int, L: int, P: int, nblk: int, ms: float, contraction: str, peaks: dict,
+                  peak_kind: str) -> dict:
+    """Roofline of the bracket of Eq. (14) over nblk blocks (its three launches together): the
+    compulsory bytes are the cross Gram operator (FP32 re/im planes, read once), w read and the
+    nulled w written; the contraction does 8 B L P L flops per block (x3 products when split-TF32)."""
+    nbytes = 8.0 * B * L * P * L + 2 * 8.0 * nblk * B * L
+    flops = 8.0 * B * L * P * L * nblk
+    hbm = float(peaks["hbm_gbs"])
+    if contraction == "tf32x3":
+        tc_peak = float(peaks["bf16_tflops"]) * 0.5
+        if nbytes / (hbm * 1e9) >= 3 * flops / (tc_peak * 1e12):
+            ach = nbytes / (ms / 1e3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": f"{peak_kind} hbm_gbs; bytes = cross Gram planes + w in + nulled w out"}
+        ach = 3 * flops / (ms / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
+                "peak_source": f"{peak_kind} bf16_tflops x 0.5 (tf32 nominal ratio); 3 split-TF32 products"}
+    fp32_peak = SMS * FP32_LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+            "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 ({peak_kind} sm_max_mhz)"}
+
+
+def run_null(args) -> None:
+    """C2N: the transform of the C2 array with beamspace nulling (Eq. (14)) of grid beams 64 and 96,
+    64 blocks per step; one step = fbst_null_execute (stage 1, the bracket of Eq. (14), stage 2)."""
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300.build import build
+    from synth import configs
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    c = configs.NULLING["C2N"]
+    nblk = args.nblk or c["nblk"]
+    d = configs.nulling_data("C2N", nblk=nblk)
+    M, B, N, ints = c["mx"], c["bx"], c["N"], c["interferers"]
+    P = len(ints)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    plan = fb.Plan(fb.make_geometry("ula", M), N, fb.make_band(c["frac_bw"], stage2=args.stage2, max_blocks=nblk))
+    info = plan.info
+    L = info.L
+    t0 = time.perf_counter()
+    nl = fb.Nulling(plan, ints, args.contraction)
+    t_create = time.perf_counter() - t0
+    y = torch.from_numpy(d["y"]).to(dev)
+    out = torch.empty((nblk, B, N), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    nl.execute(y, out, nblk)
+    if plan.sync_status() != 0:
+        raise SystemExit("device status word set after the nulled transform")
+    beams = [63, 64, 65, 96, 160, 255]
+    pb = O.make_problem("ula", M, 1, B, 1, N, frac_bw=info.fb_num / info.fb_den, epsilon=info.eps_num / info.eps_den,
+                        delta=info.delta, L=L)
+    rel_err = O.rel_l2(out[:2].cpu().numpy()[:, beams], O.fbst_nulled(pb, d["y"][:2], ints, beams=beams))
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        nl.execute(y, out, nblk)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        nl.execute(y, out, nblk)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    value = float(nblk) * B * N * args.steps / (sum(step_ms) / 1e3)
+
+    # Per-stage live timing through the C-ABI stage calls, events on the launching stream.
+    kin = min(args.steps, 200)
+    yhat = torch.empty((nblk, L, M), dtype=torch.complex64, device=dev)
+    wbuf = torch.empty((nblk, B, L), dtype=torch.complex64, device=dev)
+    wt = torch.empty_like(wbuf)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(kin)]
+    for i in range(kin):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.czt_time(y, yhat, nblk)
+        ev[i][1].record(stream)
+        plan.czt_space(yhat, wbuf, nblk)
+        ev[i][2].record(stream)
+        nl.apply(wbuf, wt, nblk)
+        ev[i][3].record(stream)
+        plan.toeplitz_apply(wt, out, nblk)
+        ev[i][4].record(stream)
+    torch.cuda.synchronize()
+    names = ["czt_time", "czt_space", "null_bracket", "stage2"]
+    kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
+
+    # End to end through the public API: pinned host input copied in, the nulled transform, the
+    # result copied back to pinned host memory, all on the stream and inside the timed region.
+    y_host = torch.from_numpy(d["y"]).pin_memory()
+    out_host = torch.empty((nblk, B, N), dtype=torch.complex64).pin_memory()
+    e2e_t = []
+    for i in range(min(args.steps, 200) + 3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y.copy_(y_host, non_blocking=True)
+        nl.execute(y, out, nblk)
+        out_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 3:
+            e2e_t.append(time.perf_counter() - t0)
+
+    peaks, peak_kind = load_peaks()
+    roofs = {k: roofline(k, info, nblk, v, peaks, peak_kind) for k, v in kern_ms.items() if k != "null_bracket"}
+    roofs["null_bracket"] = null_roofline(B, L, P, nblk, kern_ms["null_bracket"], args.contraction, peaks, peak_kind)
+    dom = max(kern_ms, key=kern_ms.get)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        sb = [int(b) for b in np.linspace(0, B - 1, 32).astype(int)]
+        t0 = time.perf_counter()
+        fac = O.NullingFactors(pb, ints, sb)
+        t_fac = time.perf_counter() - t0
+        done, t_exec = 0, 0.0
+        while t_exec < 10.0 or done == 0:
+            t0 = time.perf_counter()
+            O.fbst_nulled(pb, d["y"][:4], ints, factors=fac)
+            t_exec += time.perf_counter() - t0
+            done += 1
+        cpu = {"value": done * 4 * len(sb) * N / t_exec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} x (4 blocks x 32 of {B} beams) of C2N, FP64 numpy oracle of Eq. (14), "
+                         f"per-plan factors and cross Gram matrices ({t_fac:.1f} s) excluded"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32 stage 1, {args.contraction} nulling contraction with FP64 interferer solves, "
+                 f"{fb.STAGE2_NAMES[info.stage2]} stage 2",
+        "data": "synthetic",
+        "config": {"workload": f"C2N: ULA M={M} B={B} N={N} L={L} fb={c['frac_bw']}, beamspace nulling (Eq. (14)) "
+                               f"of grid beams {ints}, {nblk} blocks/step, complex64",
+                   "M": M, "B": B, "N": N, "L": L, "interferers": ints, "nblk_per_gpu": nblk,
+                   "stage2": fb.STAGE2_NAMES[info.stage2], "contraction": args.contraction,
+                   "l2": "flushed before every timed step (256 MiB write, untimed)", "parallelism": "replicas x1"},
+        "rel_err_vs_oracle": rel_err,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "roofline": dict(roofs[dom], kernel=dom, traffic=None),
+        "kernels_ms": kern_ms,
+        "kernels_roofline": roofs,
+        "e2e": {"value": float(nblk) * B * N * len(e2e_t) / sum(e2e_t), "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},
+        "gpu_launches": nl.launch_count(nblk) * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "nulling_create_s": t_create,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    nl.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -352,6 +518,7 @@ def main() -> None:
     ap.add_argument("--stage2", default="dense_tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--contraction", default="tf32x3", choices=["tf32x3", "fp32"])
     ap.add_argument("--rates", default="1e2,3e2,1e3,3e3,1e4,3e4,1e5")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--streams", type=int, default=3)
@@ -368,6 +535,9 @@ def main() -> None:
         return
     if args.workload == "C5":
         run_c5(args)
+        return
+    if args.workload == "C2N":
+        run_null(args)
         return
 
     import torch

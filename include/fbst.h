@@ -251,6 +251,58 @@ int fbst_set_shapes(fbst_plan_t p, int time_E, int time_G, int space_E, int spac
 /* Read the shapes of the Sec. IV kernels in use into shapes4: {time_E, time_G, space_E, space_G}. */
 int fbst_get_shapes(fbst_plan_t p, int* shapes4);
 
+/* ---------------------------------------------------------------------------------------------
+ * Beamspace interference nulling (Sec. VI-B, Eq. (14)). For interferer beams p_1..p_P of a plan's
+ * grid, every output beam b of that plan becomes
+ *     bhat_b = F_u A_b^{-1} ( w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j} ),   w = F^H y,
+ * the paper's G_{p} w_{p} applied as the product of its two factors. By the derivation of Eq. (14)
+ * this is the plain transform of the measurements after each interferer's regularised projection
+ * y - F_p (F_p^H F_p + delta I)^{-1} F_p^H y has been subtracted. The nulling object holds, in its
+ * own device memory, the cross Gram matrices F_b^H F_{p_j} (B x L x P*L) built from their closed
+ * form and the FP64 Gohberg-Semencul spectra of every A_{p_j}^{-1} (from the plan's FP64
+ * generators). At run time A_{p_j}^{-1} w_{p_j} is applied in FP64 (A_p has a condition number of
+ * about 2/delta_rel, which an FP32 product would pass on to the nulled beams); the contraction with
+ * the cross Gram matrices runs on the split-TF32 tensor-core kernel of the dense stage 2 or on its
+ * FP32 CUDA-core kernel.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fbst_null_s* fbst_null_t;
+
+typedef enum {
+  FBST_NULL_TF32X3 = 0,  /* contraction on the tensor cores, split TF32 (FP32-class accuracy) */
+  FBST_NULL_FP32 = 1     /* contraction on the FP32 CUDA cores */
+} fbst_null_contraction;
+
+/* Build the nulling of `P` interferer beams (1 <= P <= 16; distinct grid indices in [0, B), read
+ * from the host array `interferers`) for plan `p`, on the current device; plan-time kernels run
+ * on `stream`, which the call synchronises. The plan must outlive the nulling object, and the two
+ * must not run concurrently (they share the plan's workspace and status word). Device memory:
+ * 8*B*L*P*L bytes of operator (held once; twice during the call), 32*P*P_gs bytes of spectra,
+ * 8*max_blocks*(B*P*L + B*L) bytes of workspace.
+ * FBST_ERR_INVALID for bad arguments, FBST_ERR_UNSUPPORTED when P*L is not a multiple of 8 for the
+ * tensor-core contraction or the exact phase reductions would leave 64-bit range, FBST_ERR_OOM /
+ * FBST_ERR_CUDA on allocation or launch failure, FBST_ERR_NUMERIC if a generator is not usable. */
+int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction,
+                     void* stream);
+
+/* The bracket of Eq. (14) alone: w (device, [nblk][B][L], as fbst_czt writes it) ->
+ * wt (device, [nblk][B][L]), wt_b = w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j}. wt may equal w
+ * (in place); otherwise the two must not overlap. Asynchronous on `stream`; both pointers 16-byte
+ * aligned (else FBST_ERR_INVALID, nothing launched). */
+int fbst_null_apply(fbst_null_t n, const void* w, void* wt, int nblk, void* stream);
+
+/* The whole nulled transform: y (device, [nblk][M][N]) -> bhat (device, [nblk][B][N]) with the
+ * plan's stage 1, the bracket of Eq. (14) and the plan's stage 2. Asynchronous on `stream`;
+ * errors as fbst_execute; device-side errors are read with fbst_sync_status on the plan. */
+int fbst_null_execute(fbst_null_t n, const void* y, void* bhat, int nblk, void* stream);
+
+/* Launch accounting; no counterpart in the paper. Kernels one fbst_null_execute of nblk blocks
+ * launches (fbst_null_apply launches 3 per chunk of max_blocks); 0 for NULL or nblk <= 0. */
+int fbst_null_launch_count(fbst_null_t n, int nblk);
+
+/* Resource management; no counterpart in the paper. Free the nulling object's device memory
+ * (not the plan). Waits for outstanding work. NULL is OK. */
+int fbst_null_destroy(fbst_null_t n);
+
 #ifdef __cplusplus
 }
 #endif

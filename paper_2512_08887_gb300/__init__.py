@@ -5,6 +5,7 @@ from ._native import (  # noqa: F401
     Batch,
     Geometry,
     Info,
+    Nulling,
     Plan,
     STAGE2,
     STAGE2_NAMES,

@@ -82,7 +82,13 @@ SIGNATURES = {
     "fbst_autotune": (_I, [_VP, _I, _VP, C.POINTER(_I)]),
     "fbst_set_shapes": (_I, [_VP, _I, _I, _I, _I]),
     "fbst_get_shapes": (_I, [_VP, C.POINTER(_I)]),
+    "fbst_null_create": (_I, [C.POINTER(_VP), _VP, C.POINTER(_I), _I, _I, _VP]),
+    "fbst_null_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_null_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_null_launch_count": (_I, [_VP, _I]),
+    "fbst_null_destroy": (_I, [_VP]),
 }
+NULL_CONTRACTION = {"tf32x3": 0, "fp32": 1}
 
 _lib = None
 
@@ -287,3 +293,47 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Nulling:
+    """Beamspace interference nulling of grid beams `interferers` for `plan` (Eq. (14);
+    fbst_null_create / fbst_null_destroy). The plan must outlive this object."""
+
+    def __init__(self, plan: Plan, interferers, contraction: str = "tf32x3", stream=None):
+        self._lib = load_library()
+        self.plan = plan
+        self.interferers = [int(p) for p in interferers]
+        arr = (C.c_int * max(1, len(self.interferers)))(*self.interferers)
+        h = C.c_void_p()
+        _check(self._lib.fbst_null_create(C.byref(h), plan._h, arr, len(self.interferers),
+                                          NULL_CONTRACTION[contraction], _stream(stream)), "fbst_null_create")
+        self._h = h
+
+    def apply(self, w, wt, nblk: int, stream=None) -> None:
+        """The bracket of Eq. (14): w [nblk][B][L] -> wt [nblk][B][L] (wt may be w)."""
+        _check(self._lib.fbst_null_apply(self._h, _ptr(w), _ptr(wt), int(nblk), _stream(stream)), "fbst_null_apply")
+
+    def execute(self, y, bhat, nblk: int, stream=None) -> None:
+        """Nulled transform: y [nblk][M][N] -> bhat [nblk][B][N], complex64 device buffers."""
+        _check(self._lib.fbst_null_execute(self._h, _ptr(y), _ptr(bhat), int(nblk), _stream(stream)),
+               "fbst_null_execute")
+
+    def launch_count(self, nblk: int) -> int:
+        return int(self._lib.fbst_null_launch_count(self._h, int(nblk)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fbst_null_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -41,7 +41,7 @@ static void free_plan_memory(fbst_plan_s* p) {
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
-static int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s) {
+int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s) {
   switch (p->info.stage2) {
     case FBST_STAGE2_GS:
     case FBST_STAGE2_GS_IR1: return launch_stage2_gs(p, w, bhat, nb, s);

@@ -202,8 +202,12 @@ int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, 
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                                  cudaStream_t s);
 int stage2_launches(const fbst_plan_s* p);
+// Stage 2 of the plan's variant on w [nb][B][L] -> bhat [nb][B][N] (nb <= max_blocks).
+int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s);
 
 // Plan-time builders (plan.cu / dense_tc.cu).
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s);
 int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s);
+// In-place FP64 FFT of `rows` contiguous rows of size P (dir -1 forward, +1 unnormalised inverse).
+int fft64_rows(double2* data, int rows, int P, const double2* tw, int dir, cudaStream_t s);
 }  // namespace fbst

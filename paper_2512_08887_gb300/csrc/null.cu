@@ -1,0 +1,422 @@
+// Beamspace interference nulling (Sec. VI-B, Eq. (14)) on top of an FBST plan.
+//
+// For interferer beams p_1..p_P of the plan's grid, every output beam b gets the bracket of Eq. (14),
+//   wt_b = w_b - sum_j G_{b,j} w_{p_j},   G_{b,j} = F_b^H F_{p_j} (F_{p_j}^H F_{p_j} + delta I)^{-1},
+// applied as the product of its two factors (beta_j = A_{p_j}^{-1} w_{p_j} first), and then the
+// plan's own stage 2: bhat_b = F_u A_b^{-1} wt_b.
+//
+// Plan time, from closed forms with exact integer phase reduction:
+//   Q[b][ell][j*L + k] = (F_b^H F_{p_j})[ell, k]           B x L x P*L complex64
+//   XV64[j]            Gohberg-Semencul spectra of A_{p_j}^{-1}  P x 2 x P_gs complex128 (from the
+//                                                           plan's FP64 Levinson generators)
+// Run time, per chunk of at most max_blocks blocks:
+//   k_null_beta    beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 (Gohberg-Semencul circulants), rounded
+//                  and written as rhs[blk][b][j*L + k] = beta_j[k] for every beam b
+//   contraction    corr[blk][b][ell] = sum_{j,k} Q[b][ell][j*L + k] rhs[blk][b][j*L + k]
+//                  by the split-TF32 tensor-core kernel of the dense stage 2 (or its FP32
+//                  CUDA-core kernel), driven through a plan descriptor whose N is L and whose L
+//                  is P*L: the contraction has exactly the shape of the dense stage 2
+//   k_null_sub     wt = w - corr
+//
+// The closed form of the cross Gram matrix: with [F_b]_{(m,n),ell} =
+// exp(-2*pi*i*tau_{b,m}/fb) exp(i*omega_ell*(n - tau_{b,m})) (Eq. (6)),
+//   (F_b^H F_p)[ell,k] = D_N(2*pi*eps*(k-ell)/L) * prod_axes sum_{m<M_axis} exp(i*theta_axis*m),
+//   theta_axis = 2*pi*rho*[(u_b - u_p)/fb + eps*(ell'*u_b - k'*u_p)/L]
+// with u the beam's direction cosine along that axis and D_N(x) = sum_{n<N} exp(i*x*n). For b = p it
+// is the Toeplitz A_b - delta I of Sec. V; for b != p the carriers no longer cancel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "gs.cuh"
+#include "launch_util.cuh"
+
+namespace fbst {
+namespace {
+
+constexpr int kMaxInterferers = 16;
+
+struct null_consts {
+  int64_t en, ed;       // epsilon = en/ed
+  int64_t fp, fq;       // fb = fp/fq; rho = fp/(2 fq + fp)
+  int N, L, P;
+  int mx, my, bx, by;   // element and beam grids (linear array: my = by = 1)
+  int ip[kMaxInterferers];
+};
+
+// q reduced exactly modulo 2D into [-D, D).
+__device__ __forceinline__ int64_t red_2D(int64_t q, int64_t D) {
+  const int64_t twoD = 2 * D;
+  int64_t m = q % twoD;
+  if (m < 0) m += twoD;
+  if (m >= D) m -= twoD;
+  return m;
+}
+
+// sin(pi*q/D): exact reduction, then sin(pi - x) = sin(x) = sin(-pi - x) folds the angle into
+// [-pi/2, pi/2], so rounding it to float keeps its relative precision next to the zeros.
+__device__ __forceinline__ float sinpi_exact(int64_t q, int64_t D) {
+  int64_t r = red_2D(q, D);
+  if (2 * r > D) r = D - r;
+  else if (2 * r < -D) r = -D - r;
+  return sinpif((float)((double)r / (double)D));
+}
+
+// exp(i*pi*q/D) after the exact reduction.
+__device__ __forceinline__ float2 expipi_exact(int64_t q, int64_t D) {
+  float s, c;
+  sincospif((float)((double)red_2D(q, D) / (double)D), &s, &c);
+  return make_float2(c, s);
+}
+
+// sum_{m<count} exp(i*theta*m) with theta = pi*Y/D: count when theta = 0 mod 2*pi, else
+// exp(i*theta*(count-1)/2) sin(count*theta/2) / sin(theta/2). Each factor has period 4D in Y, so
+// Y is reduced modulo 4D first; the host checks that count*4D fits in 63 bits.
+__device__ float2 dirichlet_f(int64_t Y, int64_t D, int count) {
+  int64_t y = Y % (4 * D);
+  if (y < 0) y += 4 * D;
+  if (y % (2 * D) == 0) return make_float2((float)count, 0.f);
+  const float q = sinpi_exact((int64_t)count * y, 2 * D) / sinpi_exact(y, 2 * D);
+  const float2 ph = expipi_exact((int64_t)(count - 1) * y, 2 * D);
+  return make_float2(ph.x * q, ph.y * q);
+}
+
+// theta_axis = pi*Y/D for output grid index a and interferer grid index ap along an axis of nb
+// beams: u_a = (2a - nb)/nb, rho/fb = fq/rden and rho*eps/L = fp*en/(rden*ed*L) with
+// rden = 2 fq + fp give D = rden*ed*L*nb and
+// Y = 2*(2*fq*(a - ap)*ed*L + fp*en*(ell'*(2a - nb) - k'*(2ap - nb))).
+__device__ __forceinline__ int64_t axis_Y(const null_consts& c, int a, int ap, int nb, int64_t lp, int64_t kp) {
+  return 2 * (2 * c.fq * (int64_t)(a - ap) * c.ed * c.L + c.fp * c.en * (lp * (2 * a - nb) - kp * (2 * ap - nb)));
+}
+
+// T[d + L - 1] = D_N(2*pi*eps*d/L) for d = -(L-1)..L-1 (the time factor, a function of k - ell).
+__global__ void k_null_time(float2* T, null_consts c) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * c.L - 1; i += gridDim.x * blockDim.x)
+    T[i] = dirichlet_f(2 * c.en * (int64_t)(i - (c.L - 1)), c.ed * c.L, c.N);
+}
+
+// Q[b][ell][j*L + k] = (F_b^H F_{p_j})[ell, k]. Grid (x: entries of a row, y: ell, z: b).
+__global__ void k_null_Q(float2* __restrict__ Q, const float2* __restrict__ T, const __grid_constant__ null_consts c) {
+  const int ell = blockIdx.y, b = blockIdx.z, L = c.L, PL = c.P * c.L;
+  const int64_t rden = 2 * c.fq + c.fp;
+  const int a = b / c.by, cy = b % c.by;
+  const int64_t lp = (int64_t)ell + 1 - L / 2;
+  const bool two_axes = c.my > 1 || c.by > 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < PL; e += gridDim.x * blockDim.x) {
+    const int j = e / L, k = e - j * L;
+    const int pb = c.ip[j], ap = pb / c.by, cp = pb % c.by;
+    const int64_t kp = (int64_t)k + 1 - L / 2;
+    float2 v = cmul(T[k - ell + L - 1],
+                    dirichlet_f(axis_Y(c, a, ap, c.bx, lp, kp), rden * c.ed * L * c.bx, c.mx));
+    if (two_axes) v = cmul(v, dirichlet_f(axis_Y(c, cy, cp, c.by, lp, kp), rden * c.ed * L * c.by, c.my));
+    Q[((size_t)b * L + ell) * PL + e] = v;
+  }
+}
+
+// Gohberg-Semencul spectra of the interferers' A_p^{-1} (Sec. V) in FP64, before their forward FFT:
+// row 2j holds x / (sqrt(x_0) P) and row 2j+1 holds Z J conj(x) / (sqrt(x_0) P), both zero-padded
+// to P, with x the plan's FP64 first column of A_{p_j}^{-1}.
+__global__ void k_null_gs_rows(const double2* __restrict__ x64, double2* __restrict__ rows, null_consts c, int P,
+                               int* status) {
+  const int j = blockIdx.y, L = c.L;
+  const double2* x = x64 + (size_t)c.ip[j] * L;
+  const double x0 = x[0].x;
+  if (!(x0 > 0.0)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(status, (int)FBST_ERR_NUMERIC);
+    return;
+  }
+  const double sc = 1.0 / (sqrt(x0) * P);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x) {
+    rows[((size_t)j * 2 + 0) * P + k] = k < L ? cscale(x[k], sc) : make_double2(0.0, 0.0);
+    rows[((size_t)j * 2 + 1) * P + k] = (k >= 1 && k < L) ? cscale(cconj(x[L - k]), sc) : make_double2(0.0, 0.0);
+  }
+}
+
+template <int PG> struct gs64_e { static constexpr int value = PG >= 2048 ? 16 : (PG >= 8 ? 8 : 2); };
+
+// beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 through the circulants of size PG >= 2L - 1 (the
+// explicit inverse would cost O(L^2) and, rounded to FP32, loses about kappa(A) in accuracy), then
+// rounded to complex64 and written as the right-hand side of every output beam:
+// rhs[blk][b][j*L + ell] = beta_j[ell]. One CTA per (blk, j).
+template <int PG>
+__global__ void __launch_bounds__(PG / gs64_e<PG>::value)
+k_null_beta(const double2* __restrict__ XV64, const float2* __restrict__ w, float2* __restrict__ rhs,
+            const __grid_constant__ null_consts c, int B, const double2* __restrict__ tw) {
+  constexpr int E = gs64_e<PG>::value, T = PG / E;
+  extern __shared__ double2 sm64[];
+  const int blk = blockIdx.x, j = blockIdx.y, t = threadIdx.x, L = c.L, PL = c.P * c.L;
+  const double2* Xj = XV64 + (size_t)j * 2 * PG;
+  const float2* wp = w + ((size_t)blk * B + c.ip[j]) * L;
+  double2 v[E], X[E], Vv[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = t + T * r;
+    const float2 a = i < L ? wp[i] : make_float2(0.f, 0.f);
+    v[r] = make_double2(a.x, a.y);
+    X[r] = Xj[i];
+    Vv[r] = Xj[PG + i];
+  }
+  gs_apply<PG, E>(v, X, Vv, sm64, tw, t, L);
+  float2 bf[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) bf[r] = make_float2((float)v[r].x, (float)v[r].y);
+  float2* out = rhs + (size_t)blk * B * PL + (size_t)j * L;
+  for (int b = 0; b < B; ++b) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int i = t + T * r;
+      if (i < L) out[(size_t)b * PL + i] = bf[r];
+    }
+  }
+}
+
+template <int PG>
+int launch_beta_P(const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int nb,
+                  const double2* tw, cudaStream_t s) {
+  constexpr int E = gs64_e<PG>::value;
+  const size_t smem = 2 * sizeof(double2) * fft_smem_elems<double2>(PG);
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_beta<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_null_beta<PG><<<dim3(nb, c.P), PG / E, smem, s>>>(XV64, w, rhs, c, B, tw);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+int launch_beta(int PG, const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int nb,
+                const double2* tw, cudaStream_t s) {
+  switch (PG) {
+    case 16: return launch_beta_P<16>(XV64, w, rhs, c, B, nb, tw, s);
+    case 32: return launch_beta_P<32>(XV64, w, rhs, c, B, nb, tw, s);
+    case 64: return launch_beta_P<64>(XV64, w, rhs, c, B, nb, tw, s);
+    case 128: return launch_beta_P<128>(XV64, w, rhs, c, B, nb, tw, s);
+    case 256: return launch_beta_P<256>(XV64, w, rhs, c, B, nb, tw, s);
+    case 512: return launch_beta_P<512>(XV64, w, rhs, c, B, nb, tw, s);
+    case 1024: return launch_beta_P<1024>(XV64, w, rhs, c, B, nb, tw, s);
+    case 2048: return launch_beta_P<2048>(XV64, w, rhs, c, B, nb, tw, s);
+    case 4096: return launch_beta_P<4096>(XV64, w, rhs, c, B, nb, tw, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+// wt = w - corr over n4 float4 (two complex values each); wt may be w.
+__global__ void k_null_sub(const float4* w, const float4* __restrict__ corr, float4* wt, long long n4) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const float4 a = w[i], b = corr[i];
+    wt[i] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+  }
+}
+
+int stream_grid(long long items, int threads) {
+  return (int)std::max<long long>(1, std::min<long long>((items + threads - 1) / threads, (long long)sm_count() * 8));
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FBST_ERR_OOM : FBST_ERR_CUDA;
+  }
+  return FBST_OK;
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+}  // namespace
+}  // namespace fbst
+
+using namespace fbst;
+
+struct fbst_null_s {
+  fbst_plan_s* plan;     // the plan whose grid, workspace and stage 2 are used (not owned)
+  int P;
+  int contraction;       // FBST_NULL_TF32X3 or FBST_NULL_FP32
+  fbst_plan_s shadow;    // descriptor of the Q contraction for the dense stage-2 kernels
+  float2* T;             // [2L - 1] time factor (plan time only)
+  float2* Q;             // [B][L][P*L]; freed once the tensor-core planes are built
+  double2* XV64;         // [P][2][P_gs] Gohberg-Semencul spectra of the interferers, FP64
+  float2* rhs;           // [max_blocks][B][P*L]
+  float2* corr;          // [max_blocks][B][L]
+  null_consts c;
+};
+
+static void free_null(fbst_null_s* n) {
+  void* ptrs[] = {n->T, n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+// One chunk (nb <= max_blocks) of the bracket of Eq. (14): w [nb][B][L] -> wt (may be w).
+static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaStream_t s) {
+  const fbst_info& in = n->plan->info;
+  const int L = in.L, B = in.B;
+  FBST_TRY(launch_beta(in.P_gs, n->XV64, w, n->rhs, n->c, B, nb, n->plan->tw64, s));
+  const int r = n->contraction == FBST_NULL_TF32X3 ? launch_stage2_dense_tc(&n->shadow, n->rhs, n->corr, nb, s)
+                                                   : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
+  if (r != FBST_OK) return r;
+  const long long n4 = (long long)nb * B * L / 2;
+  k_null_sub<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
+                                                  reinterpret_cast<const float4*>(n->corr),
+                                                  reinterpret_cast<float4*>(wt), n4);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+extern "C" {
+
+int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction, void* stream) {
+  if (!out) return FBST_ERR_INVALID;
+  *out = nullptr;
+  if (!p || !interferers || P < 1 || P > kMaxInterferers) return FBST_ERR_INVALID;
+  if (contraction != FBST_NULL_TF32X3 && contraction != FBST_NULL_FP32) return FBST_ERR_INVALID;
+  const fbst_info& in = p->info;
+  const int L = in.L, B = in.B;
+  for (int j = 0; j < P; ++j) {
+    if (interferers[j] < 0 || interferers[j] >= B) return FBST_ERR_INVALID;
+    for (int i = 0; i < j; ++i)
+      if (interferers[i] == interferers[j]) return FBST_ERR_INVALID;
+  }
+  // 64-bit headroom of the exact phase reductions: |Y| and count * 4D of every Dirichlet sum.
+  {
+    const long double lim = std::ldexp(1.0L, 62);
+    const long double rden = 2.0L * in.fb_den + in.fb_num;
+    const int ax_n[2] = {p->geom.bx, p->geom.by}, ax_m[2] = {p->geom.mx, p->geom.my};
+    for (int a = 0; a < 2; ++a) {
+      const long double D = rden * in.eps_den * L * ax_n[a];
+      const long double Y = 2.0L * (2.0L * in.fb_den * ax_n[a] * in.eps_den * L +
+                                    (long double)in.fb_num * in.eps_num * (L / 2 + 1) * 2.0L * ax_n[a]);
+      if (Y >= lim || 4.0L * D * ax_m[a] >= lim) return FBST_ERR_UNSUPPORTED;
+    }
+    if (4.0L * in.eps_den * L * in.N >= lim) return FBST_ERR_UNSUPPORTED;
+  }
+  if (contraction == FBST_NULL_TF32X3 && ((size_t)P * L) % 8 != 0) return FBST_ERR_UNSUPPORTED;
+
+  fbst_null_s* n = new (std::nothrow) fbst_null_s();
+  if (!n) return FBST_ERR_OOM;
+  std::memset(n, 0, sizeof(*n));
+  n->plan = p;
+  n->P = P;
+  n->contraction = contraction;
+  null_consts& c = n->c;
+  c.en = in.eps_num;
+  c.ed = in.eps_den;
+  c.fp = in.fb_num;
+  c.fq = in.fb_den;
+  c.N = in.N;
+  c.L = L;
+  c.P = P;
+  c.mx = p->geom.mx;
+  c.my = p->geom.my;
+  c.bx = p->geom.bx;
+  c.by = p->geom.by;
+  for (int j = 0; j < P; ++j) c.ip[j] = interferers[j];
+
+  // The contraction's descriptor: the dense stage-2 kernels with N := L and L := P*L.
+  fbst_plan_s& sh = n->shadow;
+  sh.info = in;
+  sh.info.N = L;
+  sh.info.L = P * L;
+  sh.info.stage2 = contraction == FBST_NULL_TF32X3 ? FBST_STAGE2_DENSE_TF32X3 : FBST_STAGE2_DENSE_FP32;
+  sh.geom = p->geom;
+  sh.band = p->band;
+  sh.device = p->device;
+  sh.d_status = p->d_status;
+
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int maxb = p->band.max_blocks;
+  int r = FBST_OK;
+  do {
+    if ((r = dalloc(&n->T, 2 * (size_t)L - 1)) != FBST_OK) break;
+    if ((r = dalloc(&n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
+    if ((r = dalloc(&n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
+    if ((r = dalloc(&n->rhs, (size_t)maxb * B * P * L)) != FBST_OK) break;
+    if ((r = dalloc(&n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
+    k_null_time<<<(2 * L + 254) / 256, 256, 0, s>>>(n->T, c);
+    k_null_Q<<<dim3(std::min((P * L + 255) / 256, 8), L, B), 256, 0, s>>>(n->Q, n->T, c);
+    k_null_gs_rows<<<dim3(std::min((in.P_gs + 255) / 256, 16), P), 256, 0, s>>>(p->x64, n->XV64, c, in.P_gs,
+                                                                                p->d_status);
+    if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    if ((r = fft64_rows(n->XV64, 2 * P, in.P_gs, p->tw64, -1, s)) != FBST_OK) break;
+    sh.G = n->Q;
+    if (contraction == FBST_NULL_TF32X3) {
+      if ((r = build_dense_tc_operand(&sh, s)) != FBST_OK) break;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    int st = 0;
+    if (cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    if (st != 0) {
+      cudaMemset(p->d_status, 0, sizeof(int));
+      r = st;
+      break;
+    }
+    cudaFree(n->T);
+    n->T = nullptr;
+    if (contraction == FBST_NULL_TF32X3) {
+      cudaFree(n->Q);
+      n->Q = nullptr;
+      sh.G = nullptr;
+    }
+  } while (0);
+  if (r != FBST_OK) {
+    cudaStreamSynchronize(s);
+    free_null(n);
+    delete n;
+    return r;
+  }
+  *out = n;
+  return FBST_OK;
+}
+
+int fbst_null_apply(fbst_null_t n, const void* w, void* wt, int nblk, void* stream) {
+  if (!n || nblk < 0) return FBST_ERR_INVALID;
+  if (nblk == 0) return FBST_OK;
+  if (!w || !wt || !aligned16(w) || !aligned16(wt)) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = n->plan->info;
+  const int maxb = n->plan->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    const size_t off = (size_t)c0 * in.B * in.L;
+    FBST_TRY(null_chunk(n, static_cast<const float2*>(w) + off, static_cast<float2*>(wt) + off, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_null_execute(fbst_null_t n, const void* y, void* bhat, int nblk, void* stream) {
+  if (!n || nblk < 0) return FBST_ERR_INVALID;
+  if (nblk == 0) return FBST_OK;
+  if (!y || !bhat || !aligned16(y) || !aligned16(bhat)) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  fbst_plan_s* p = n->plan;
+  const fbst_info& in = p->info;
+  const int maxb = p->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
+    FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nb, s));
+    FBST_TRY(null_chunk(n, p->ws_w, p->ws_w, nb, s));
+    FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s));
+  }
+  return FBST_OK;
+}
+
+int fbst_null_launch_count(fbst_null_t n, int nblk) {
+  if (!n || nblk <= 0) return 0;
+  const int maxb = n->plan->band.max_blocks;
+  const int chunks = (nblk + maxb - 1) / maxb;
+  return chunks * (2 + 3 + stage2_launches(n->plan));
+}
+
+int fbst_null_destroy(fbst_null_t n) {
+  if (!n) return FBST_OK;
+  cudaDeviceSynchronize();
+  free_null(n);
+  delete n;
+  return FBST_OK;
+}
+
+}  // extern "C"

@@ -533,7 +533,7 @@ static int fft64_rows_P(double2* data, int rows, const double2* tw, int dir, cud
   return FBST_OK;
 }
 
-static int fft64_rows(double2* data, int rows, int P, const double2* tw, int dir, cudaStream_t s) {
+int fft64_rows(double2* data, int rows, int P, const double2* tw, int dir, cudaStream_t s) {
   switch (P) {
     case 16: return fft64_rows_P<16>(data, rows, tw, dir, s);
     case 32: return fft64_rows_P<32>(data, rows, tw, dir, s);

@@ -53,3 +53,25 @@ def test_fft_kernels_are_reported_against_the_fp32_alu_peak():
     per_sensor = 3 * 5 * 512 * 9 + 6 * (256 + 2 * 512 + 512)
     assert b.flop_model(C2)["czt_time"] == per_sensor * 256
     assert r["achieved"] == pytest.approx(per_sensor * 256 * 64 / 0.0765e-3 / 1e12)
+
+
+def test_nulling_bracket_roofline():
+    b = _bench()
+    # C2N: B = 256, L = 512, two interferers, 64 blocks. Operator planes 8 B L P L = 1073741824 bytes,
+    # w in + nulled w out 2 x 8 x 64 x 256 x 512 = 134217728 bytes: 180.5 us at 6690.8 GB/s, against
+    # 3 x 8 B L P L nblk = 3 x 68.72 GFLOP = 209.1 us at 986.1 TFLOP/s: tensor-bound.
+    flops = 8 * 256 * 512 * 2 * 512 * 64
+    assert flops == 68719476736
+    r = b.null_roofline(256, 512, 2, 64, 0.25, "tf32x3", PEAKS, "measured")
+    assert r["bound"] == "tensor" and r["peak"] == pytest.approx(986.1)
+    assert r["achieved"] == pytest.approx(3 * flops / 0.25e-3 / 1e12)
+    # One interferer: 80.2 us of operator + 20.1 us of w against 104.5 us of tensor work: still
+    # tensor-bound; at a slower memory (3000 GB/s) the same launch is HBM-bound.
+    r = b.null_roofline(256, 512, 1, 64, 0.2, "tf32x3", PEAKS, "measured")
+    assert r["bound"] == "tensor"
+    r = b.null_roofline(256, 512, 1, 64, 0.2, "tf32x3", dict(PEAKS, hbm_gbs=3000.0), "measured")
+    assert r["bound"] == "hbm" and r["peak"] == 3000.0
+    assert r["achieved"] == pytest.approx((8 * 256 * 512 * 512 + 2 * 8 * 64 * 256 * 512) / 0.2e-3 / 1e9)
+    # The FP32 CUDA-core contraction is reported against the FP32 ALU peak.
+    r = b.null_roofline(256, 512, 2, 64, 1.0, "fp32", PEAKS, "measured")
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
