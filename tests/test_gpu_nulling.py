@@ -1,13 +1,21 @@
 """Parity of the beamspace interference nulling (Sec. VI-B, Eq. (14)) through the C ABI with the
 FP64 oracle, on seeded scenes with interferers 20 dB above the source.
 
-Tolerances, from the arithmetic. The stored operands are complex64 (the cross Gram matrices and
-the right-hand sides A_p^{-1} w_p, the latter computed in FP64 and then rounded), the contraction
-accumulates in FP32 over P*L terms, and the correction cancels most of w_p at the interferer beam.
-An emulation of exactly these roundings in numpy gives, on the cases below, a relative L2 error
-of the nulled coefficients of 1.3e-6 to 2.3e-6 and at most 3e-7 of |w_b| on any beam; the tests
-allow 1e-5 and 2e-6. The end-to-end bar is the transform's own: 1e-5 relative L2 over all beams
-(emulated: 4.5e-6 at M = N = B = 64 with two interferers). Outputs are poisoned with NaN first.
+Tolerances, from the arithmetic. Nulling subtracts from each w_b a correction as large as the
+interferer's contribution, so FP32 errors are set by the size of the operands, not of the (much
+smaller) difference: they are measured here against the input scale.
+
+* The bracket of Eq. (14) (fbst_null_apply, on the oracle's w rounded to complex64): the stored
+  operands are complex64 (cross Gram matrices; A_p^{-1} w_p computed in FP64, then rounded) and the
+  contraction accumulates in FP32 over P*L terms of split-TF32 products (2^-21 relative each). An
+  emulation of the complex64 roundings gives at most 3e-7 of |w_b| on any beam; the bound is 5e-6
+  of |w_b| per beam and of ||w|| over the array.
+* End to end (fbst_null_execute from y): stage 1 leaves FP32 errors in w_b and w_p that no longer
+  cancel once the interferer is subtracted, so the nulled output inherits the plain transform's
+  absolute error. The bar is the transform's own, 1e-5, relative to the plain transform's output
+  of the same input (an emulation with stage-1-sized errors: 5e-7 of the plain output, 2e-6 of the
+  nulled one, with interferers 20 dB above the source).
+Outputs are poisoned with NaN first.
 """
 import numpy as np
 import pytest
@@ -18,9 +26,9 @@ from synth import configs, interference_config
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL_BRACKET = 1e-5
-TOL_BRACKET_BEAM = 2e-6
-TOL_E2E = 1e-5
+TOL_BRACKET = 5e-6       # of ||w||
+TOL_BRACKET_BEAM = 5e-6  # of |w_b|
+TOL_E2E = 1e-5           # of the plain transform's output
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,9 +93,9 @@ def test_bracket_of_eq14_matches_oracle(case, contraction):
     got = out.cpu().numpy()
     w64 = w.astype(np.complex128)
     ref = O.NullingFactors(pb, ints).coefficients(w64, w64[:, ints])
-    err = O.rel_l2(got, ref)
-    assert err < TOL_BRACKET, err
+    err = np.linalg.norm(got - ref) / np.linalg.norm(w64)
     per = np.linalg.norm(got - ref, axis=(0, 2)) / np.linalg.norm(w64, axis=(0, 2))
+    assert err < TOL_BRACKET, (err, O.rel_l2(got, ref))
     assert per.max() < TOL_BRACKET_BEAM, (per.max(), int(per.argmax()))
 
 
@@ -116,9 +124,10 @@ def test_nulled_transform_matches_oracle(case, contraction, stage2):
         nl.execute(dev(y), out, nblk)
         assert plan.sync_status() == 0
         assert nl.launch_count(nblk) == 2 * (5 + (1 if stage2 in ("auto", "dense_tf32x3") else 2))
+    got = out.cpu().numpy()
     ref = O.fbst_nulled(pb, y, ints)
-    err = O.rel_l2(out.cpu().numpy(), ref)
-    assert err < TOL_E2E, err
+    err = np.linalg.norm(got - ref) / np.linalg.norm(O.fbst(pb, y))
+    assert err < TOL_E2E, (err, O.rel_l2(got, ref))
 
 
 def test_interferer_removed_on_the_gpu():
@@ -151,8 +160,8 @@ def test_full_size_workload_on_sampled_beams():
     assert np.isfinite(got).all()
     beams = [63, 64, 65, 96, 160, 255]
     ref = O.fbst_nulled(pb, d["y"][:2], c["interferers"], beams=beams)
-    err = O.rel_l2(got[:2, beams], ref)
-    assert err < TOL_E2E, err
+    err = np.linalg.norm(got[:2, beams] - ref) / np.linalg.norm(O.fbst(pb, d["y"][:2], beams=beams))
+    assert err < TOL_E2E, (err, O.rel_l2(got[:2, beams], ref))
 
 
 def test_invalid_arguments_are_rejected():
