@@ -277,7 +277,7 @@ typedef enum {
  * on `stream`, which the call synchronises. The plan must outlive the nulling object, and the two
  * must not run concurrently (they share the plan's workspace and status word). Device memory:
  * 8*B*L*P*L bytes of operator (held once; twice during the call), 32*P*P_gs bytes of spectra,
- * 8*max_blocks*(B*P*L + B*L) bytes of workspace.
+ * 8*max_blocks*(P*L + B*L) bytes of workspace (8*max_blocks*(B*P*L + B*L) for FBST_NULL_FP32).
  * FBST_ERR_INVALID for bad arguments, FBST_ERR_UNSUPPORTED when P*L is not a multiple of 8 for the
  * tensor-core contraction or the exact phase reductions would leave 64-bit range, FBST_ERR_OOM /
  * FBST_ERR_CUDA on allocation or launch failure, FBST_ERR_NUMERIC if a generator is not usable. */

@@ -201,6 +201,9 @@ int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, 
 // The TF32x3 operator for beams [b0, b0 + nbeam) only (FBST_ERR_UNSUPPORTED for other variants).
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                                  cudaStream_t s);
+// The TF32x3 operator of every beam applied to one right-hand side per block, w [nblk][L] (the
+// same for all beams); bhat [nblk][B][N].
+int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 int stage2_launches(const fbst_plan_s* p);
 // Stage 2 of the plan's variant on w [nb][B][L] -> bhat [nb][B][N] (nb <= max_blocks).
 int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s);

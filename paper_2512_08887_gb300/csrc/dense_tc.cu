@@ -478,7 +478,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 template <int NB, bool PERSIST>
 __global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
-                 float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int* status) {
+                 float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int w_beam_mul,
+                 int* status) {
   using SM = fused_smem<NB>;
   constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
   constexpr int KELEM = kRowBytes / 4;  // 32 FP32 values of K per chunk
@@ -610,8 +611,8 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         mbar_expect_tx(&full[s], SM::RAW_BYTES);
         tma_load_3d(st, &mapA, &full[s], c * KELEM, m0, b * 2 + 0);
         tma_load_3d(st + SM::A_TILE, &mapA, &full[s], c * KELEM, m0, b * 2 + 1);
-        tma_load_3d(st + 2 * SM::A_TILE, &mapW, &full[s], 2 * c * KELEM, b, blk0);
-        tma_load_3d(st + 2 * SM::A_TILE + SM::W_BOX, &mapW, &full[s], 2 * c * KELEM + KELEM, b, blk0);
+        tma_load_3d(st + 2 * SM::A_TILE, &mapW, &full[s], 2 * c * KELEM, b * w_beam_mul, blk0);
+        tma_load_3d(st + 2 * SM::A_TILE + SM::W_BOX, &mapW, &full[s], 2 * c * KELEM + KELEM, b * w_beam_mul, blk0);
         issued = gc + 1;
       }
     }
@@ -915,12 +916,13 @@ static int launch_V(const fbst_plan_s* p, const float2* w, float2* bhat, int nbl
 
 template <int NB>
 static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
-                      cudaStream_t s) {
+                      bool shared_rhs, cudaStream_t s) {
   const fbst_info& in = p->info;
   CUtensorMap mapA, mapW;
   int r = make_map(&mapA, p->Gtc, 4, in.L, in.N, (uint64_t)in.B * 2, kTileM);
   if (r != FBST_OK) return r;
-  r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, in.B, nblk, NB);
+  // A shared right-hand side is one row per block that every beam reads (beam coordinate 0).
+  r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, shared_rhs ? 1 : in.B, nblk, NB);
   if (r != FBST_OK) return r;
   // NB >= 32: one CTA per SM is all that shared and tensor memory allow, so it is persistent and
   // walks its tiles. NB = 16: two single-tile CTAs (256 threads, 256 tensor-memory columns) fit
@@ -933,17 +935,25 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
   const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
   k_dense_tc_fused<NB, kPersist><<<grid, kPersist ? 384 : 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk,
-                                                                           b0, nbeam, p->d_status);
+                                                                           b0, nbeam, shared_rhs ? 0 : 1,
+                                                                           p->d_status);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
 static int launch_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool shared_rhs = false) {
   const int want = std::min(round16(nblk), 64);
-  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, b0, nbeam, s);
-  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, b0, nbeam, s);
-  return gemm_fused<64>(p, w, bhat, nblk, b0, nbeam, s);
+  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+  return gemm_fused<64>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+}
+
+int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  if (variant_of(p->info.stage2) != TC_TF32X3) return FBST_ERR_UNSUPPORTED;
+  if (nblk <= 0) return FBST_OK;
+  if (!p->Gtc) return FBST_ERR_INVALID;
+  return launch_fused(p, w, bhat, nblk, 0, p->info.B, s, true);
 }
 
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,

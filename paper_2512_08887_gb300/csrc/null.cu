@@ -11,11 +11,12 @@
 //                                                           plan's FP64 Levinson generators)
 // Run time, per chunk of at most max_blocks blocks:
 //   k_null_beta    beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 (Gohberg-Semencul circulants), rounded
-//                  and written as rhs[blk][b][j*L + k] = beta_j[k] for every beam b
-//   contraction    corr[blk][b][ell] = sum_{j,k} Q[b][ell][j*L + k] rhs[blk][b][j*L + k]
-//                  by the split-TF32 tensor-core kernel of the dense stage 2 (or its FP32
-//                  CUDA-core kernel), driven through a plan descriptor whose N is L and whose L
-//                  is P*L: the contraction has exactly the shape of the dense stage 2
+//                  and written as the right-hand side rhs[blk][j*L + k] = beta_j[k]
+//   contraction    corr[blk][b][ell] = sum_{j,k} Q[b][ell][j*L + k] rhs[blk][j*L + k]
+//                  by the split-TF32 tensor-core kernel of the dense stage 2, reading one shared
+//                  right-hand side for every beam (or by its FP32 CUDA-core kernel, from one copy
+//                  per beam), driven through a plan descriptor whose N is L and whose L is P*L:
+//                  the contraction has the shape of the dense stage 2
 //   k_null_sub     wt = w - corr
 //
 // The closed form of the cross Gram matrix: with [F_b]_{(m,n),ell} =
@@ -138,12 +139,13 @@ template <int PG> struct gs64_e { static constexpr int value = PG >= 2048 ? 16 :
 
 // beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 through the circulants of size PG >= 2L - 1 (the
 // explicit inverse would cost O(L^2) and, rounded to FP32, loses about kappa(A) in accuracy), then
-// rounded to complex64 and written as the right-hand side of every output beam:
-// rhs[blk][b][j*L + ell] = beta_j[ell]. One CTA per (blk, j).
+// rounded to complex64 and written `copies` times: rhs[blk][c][j*L + ell] = beta_j[ell] for c <
+// copies (1 for the tensor-core contraction, which reads one right-hand side for all beams; B for
+// the CUDA-core one, which reads one per beam). One CTA per (blk, j).
 template <int PG>
 __global__ void __launch_bounds__(PG / gs64_e<PG>::value)
 k_null_beta(const double2* __restrict__ XV64, const float2* __restrict__ w, float2* __restrict__ rhs,
-            const __grid_constant__ null_consts c, int B, const double2* __restrict__ tw) {
+            const __grid_constant__ null_consts c, int B, int copies, const double2* __restrict__ tw) {
   constexpr int E = gs64_e<PG>::value, T = PG / E;
   extern __shared__ double2 sm64[];
   const int blk = blockIdx.x, j = blockIdx.y, t = threadIdx.x, L = c.L, PL = c.P * c.L;
@@ -162,8 +164,8 @@ k_null_beta(const double2* __restrict__ XV64, const float2* __restrict__ w, floa
   float2 bf[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) bf[r] = make_float2((float)v[r].x, (float)v[r].y);
-  float2* out = rhs + (size_t)blk * B * PL + (size_t)j * L;
-  for (int b = 0; b < B; ++b) {
+  float2* out = rhs + (size_t)blk * copies * PL + (size_t)j * L;
+  for (int b = 0; b < copies; ++b) {
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int i = t + T * r;
@@ -173,28 +175,28 @@ k_null_beta(const double2* __restrict__ XV64, const float2* __restrict__ w, floa
 }
 
 template <int PG>
-int launch_beta_P(const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int nb,
-                  const double2* tw, cudaStream_t s) {
+int launch_beta_P(const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int copies,
+                  int nb, const double2* tw, cudaStream_t s) {
   constexpr int E = gs64_e<PG>::value;
   const size_t smem = 2 * sizeof(double2) * fft_smem_elems<double2>(PG);
   FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_beta<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_null_beta<PG><<<dim3(nb, c.P), PG / E, smem, s>>>(XV64, w, rhs, c, B, tw);
+  k_null_beta<PG><<<dim3(nb, c.P), PG / E, smem, s>>>(XV64, w, rhs, c, B, copies, tw);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
-int launch_beta(int PG, const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int nb,
-                const double2* tw, cudaStream_t s) {
+int launch_beta(int PG, const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int copies,
+                int nb, const double2* tw, cudaStream_t s) {
   switch (PG) {
-    case 16: return launch_beta_P<16>(XV64, w, rhs, c, B, nb, tw, s);
-    case 32: return launch_beta_P<32>(XV64, w, rhs, c, B, nb, tw, s);
-    case 64: return launch_beta_P<64>(XV64, w, rhs, c, B, nb, tw, s);
-    case 128: return launch_beta_P<128>(XV64, w, rhs, c, B, nb, tw, s);
-    case 256: return launch_beta_P<256>(XV64, w, rhs, c, B, nb, tw, s);
-    case 512: return launch_beta_P<512>(XV64, w, rhs, c, B, nb, tw, s);
-    case 1024: return launch_beta_P<1024>(XV64, w, rhs, c, B, nb, tw, s);
-    case 2048: return launch_beta_P<2048>(XV64, w, rhs, c, B, nb, tw, s);
-    case 4096: return launch_beta_P<4096>(XV64, w, rhs, c, B, nb, tw, s);
+    case 16: return launch_beta_P<16>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 32: return launch_beta_P<32>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 64: return launch_beta_P<64>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 128: return launch_beta_P<128>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 256: return launch_beta_P<256>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 512: return launch_beta_P<512>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 1024: return launch_beta_P<1024>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 2048: return launch_beta_P<2048>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 4096: return launch_beta_P<4096>(XV64, w, rhs, c, B, copies, nb, tw, s);
     default: return FBST_ERR_UNSUPPORTED;
   }
 }
@@ -239,7 +241,7 @@ struct fbst_null_s {
   float2* T;             // [2L - 1] time factor (plan time only)
   float2* Q;             // [B][L][P*L]; freed once the tensor-core planes are built
   double2* XV64;         // [P][2][P_gs] Gohberg-Semencul spectra of the interferers, FP64
-  float2* rhs;           // [max_blocks][B][P*L]
+  float2* rhs;           // [max_blocks][1 or B][P*L] (one copy for the tensor-core contraction)
   float2* corr;          // [max_blocks][B][L]
   null_consts c;
 };
@@ -254,9 +256,10 @@ static void free_null(fbst_null_s* n) {
 static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaStream_t s) {
   const fbst_info& in = n->plan->info;
   const int L = in.L, B = in.B;
-  FBST_TRY(launch_beta(in.P_gs, n->XV64, w, n->rhs, n->c, B, nb, n->plan->tw64, s));
-  const int r = n->contraction == FBST_NULL_TF32X3 ? launch_stage2_dense_tc(&n->shadow, n->rhs, n->corr, nb, s)
-                                                   : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
+  const bool tc = n->contraction == FBST_NULL_TF32X3;
+  FBST_TRY(launch_beta(in.P_gs, n->XV64, w, n->rhs, n->c, B, tc ? 1 : B, nb, n->plan->tw64, s));
+  const int r = tc ? launch_dense_tc_shared_rhs(&n->shadow, n->rhs, n->corr, nb, s)
+                   : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
   if (r != FBST_OK) return r;
   const long long n4 = (long long)nb * B * L / 2;
   k_null_sub<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
@@ -333,7 +336,7 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
     if ((r = dalloc(&n->T, 2 * (size_t)L - 1)) != FBST_OK) break;
     if ((r = dalloc(&n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
     if ((r = dalloc(&n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
-    if ((r = dalloc(&n->rhs, (size_t)maxb * B * P * L)) != FBST_OK) break;
+    if ((r = dalloc(&n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK) break;
     if ((r = dalloc(&n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
     k_null_time<<<(2 * L + 254) / 256, 256, 0, s>>>(n->T, c);
     k_null_Q<<<dim3(std::min((P * L + 255) / 256, 8), L, B), 256, 0, s>>>(n->Q, n->T, c);
