@@ -480,9 +480,41 @@ def run_null(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_reference_null(args) -> None:
+    """Reference arm of C2N: the FP64 oracle of Eq. (14) on one block x 16 beams per step."""
+    import oracle as O
+    from synth import configs
+    c = configs.NULLING["C2N"]
+    y = configs.nulling_data("C2N", nblk=1)["y"]
+    beams = [int(b) for b in np.linspace(0, c["bx"] - 1, 16).astype(int)]
+    pb = O.make_problem("ula", c["mx"], 1, c["bx"], 1, c["N"], frac_bw=c["frac_bw"], epsilon=1.01, delta_rel=1e-3)
+    fac = O.NullingFactors(pb, c["interferers"], beams)
+    for _ in range(args.warmup):
+        O.fbst_nulled(pb, y, c["interferers"], factors=fac)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.fbst_nulled(pb, y, c["interferers"], factors=fac)
+        times.append(time.perf_counter() - t0)
+    value = len(beams) * c["N"] * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "C2N oracle sample", "M": c["mx"], "N": c["N"], "B": c["bx"],
+                       "interferers": c["interferers"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: 1 block x 16 beams of C2N (FP64 numpy oracle of Eq. (14), "
+                                       "per-plan factors and cross Gram matrices excluded)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "C2N":
+        run_reference_null(args)
         return
     w, gen = workload(args)
     y = gen()

@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library loads, exports every symbol include/fbst.h declares, and its
 host-only parameter derivation validates input and picks the documented sizes."""
+import ctypes as C
 import os
 import re
 
@@ -92,3 +93,15 @@ def test_derive_rejects_oversized_transforms(lib):
 def test_rational_rounding(lib):
     info = fb.derive(fb.make_geometry("ula", 32), 128, fb.make_band(0.437, epsilon=1.0))
     assert (info.fb_num, info.fb_den, info.eps_num, info.eps_den) == (437, 1000, 1, 1)
+
+
+def test_nulling_entry_points_check_arguments_before_any_cuda_call(lib):
+    # The entry points of Eq. (14) reject missing handles and pointers on the host.
+    h = C.c_void_p()
+    arr = (C.c_int * 2)(1, 2)
+    assert lib.fbst_null_create(None, None, arr, 2, 0, None) == -1
+    assert lib.fbst_null_create(C.byref(h), None, arr, 2, 0, None) == -1 and not h.value
+    assert lib.fbst_null_apply(None, None, None, 1, None) == -1
+    assert lib.fbst_null_execute(None, None, None, 1, None) == -1
+    assert lib.fbst_null_launch_count(None, 4) == 0
+    assert lib.fbst_null_destroy(None) == 0
