@@ -334,6 +334,8 @@ def null_roofline(B: int, L: int, P: int, nblk: int, ms: float, contraction: str
 def run_null(args) -> None:
     """C2N: the transform of the C2 array with beamspace nulling (Eq. (14)) of grid beams 64 and 96,
     64 blocks per step; one step = fbst_null_execute (stage 1, the bracket of Eq. (14), stage 2)."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload C2N runs on one GPU (replicas of it scale like C2)")
     import torch
     import paper_2512_08887_gb300 as fb
     from paper_2512_08887_gb300.build import build
