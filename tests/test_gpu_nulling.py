@@ -1,9 +1,11 @@
 """Parity of the beamspace interference nulling (Sec. VI-B, Eq. (14)) through the C ABI with the
 FP64 oracle, on seeded scenes with interferers 20 dB above the source.
 
-Tolerances, from the arithmetic. Nulling subtracts from each w_b a correction as large as the
-interferer's contribution, so FP32 errors are set by the size of the operands, not of the (much
-smaller) difference: they are measured here against the input scale.
+Tolerances, from the arithmetic. Eq. (14) subtracts from each w_b the interferer's projected
+component (Sec. VI-B derives it from the array-space projection y - F_p (F_p^H F_p + delta I)^{-1}
+F_p^H y), a correction as large as the interferer's contribution. FP32 errors are therefore set by
+the size of the operands, not of the (much smaller) difference, and are measured here against the
+input scale.
 
 * The bracket of Eq. (14) (fbst_null_apply, on the oracle's w rounded to complex64): the stored
   operands are complex64 (cross Gram matrices; A_p^{-1} w_p computed in FP64, then rounded) and the
