@@ -252,7 +252,7 @@ int fbst_set_shapes(fbst_plan_t p, int time_E, int time_G, int space_E, int spac
 int fbst_get_shapes(fbst_plan_t p, int* shapes4);
 
 /* ---------------------------------------------------------------------------------------------
- * Beamspace interference nulling (Sec. VI-B, Eq. (14)). For interferer beams p_1..p_P of a plan's
+ * Beamspace interference nulling (Sec. VIII-B, Eq. (14)). For interferer beams p_1..p_P of a plan's
  * grid, every output beam b of that plan becomes
  *     bhat_b = F_u A_b^{-1} ( w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j} ),   w = F^H y,
  * the paper's G_{p} w_{p} applied as the product of its two factors. By the derivation of Eq. (14)

@@ -233,7 +233,7 @@ def dense_operator(pb: Problem, b: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------------
-# Beamspace interference nulling (Sec. VI-B, Eq. (14))
+# Beamspace interference nulling (Sec. VIII-B, Eq. (14))
 # ----------------------------------------------------------------------------------------------
 
 def cross_gram(pb: Problem, b: int, p: int) -> np.ndarray:

@@ -1,4 +1,4 @@
-// Beamspace interference nulling (Sec. VI-B, Eq. (14)) on top of an FBST plan.
+// Beamspace interference nulling (Sec. VIII-B, Eq. (14)) on top of an FBST plan.
 //
 // For interferer beams p_1..p_P of the plan's grid, every output beam b gets the bracket of Eq. (14),
 //   wt_b = w_b - sum_j G_{b,j} w_{p_j},   G_{b,j} = F_b^H F_{p_j} (F_{p_j}^H F_{p_j} + delta I)^{-1},

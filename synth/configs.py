@@ -9,7 +9,7 @@ C4  64 independent linear arrays, M = 2^U{5..10}, N from {128,256,512,1024}, B=M
     rounded to 1e-3, K=4 plane waves, 15 dB, one block each, per-instance child seeds of 1004.
 C2N the C2 array and grid with one unit-power source on grid beam 160 and two interferers on grid
     beams 64 and 96 at 20 dB above it, 10 dB SNR, 64 blocks; seed 1005. Workload of the beamspace
-    interference nulling (Sec. VI-B), which removes beams 64 and 96.
+    interference nulling (Sec. VIII-B), which removes beams 64 and 96.
 Every waveform is a sum of Q sinusoids with CN(0, 1/Q) weights and uniform in-band frequencies.
 """
 from __future__ import annotations

@@ -1,8 +1,8 @@
-"""Parity of the beamspace interference nulling (Sec. VI-B, Eq. (14)) through the C ABI with the
+"""Parity of the beamspace interference nulling (Sec. VIII-B, Eq. (14)) through the C ABI with the
 FP64 oracle, on seeded scenes with interferers 20 dB above the source.
 
 Tolerances, from the arithmetic. Eq. (14) subtracts from each w_b the interferer's projected
-component (Sec. VI-B derives it from the array-space projection y - F_p (F_p^H F_p + delta I)^{-1}
+component (Sec. VIII-B derives it from the array-space projection y - F_p (F_p^H F_p + delta I)^{-1}
 F_p^H y), a correction as large as the interferer's contribution. FP32 errors are therefore set by
 the size of the operands, not of the (much smaller) difference, and are measured here against the
 input scale.

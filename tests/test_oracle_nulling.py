@@ -1,4 +1,4 @@
-"""Pins of the oracle's beamspace interference nulling (Sec. VI-B, Eq. (14)); no GPU needed.
+"""Pins of the oracle's beamspace interference nulling (Sec. VIII-B, Eq. (14)); no GPU needed.
 
 Eq. (14) is derived in the paper from an array-space projection: nulling in beamspace equals the
 plain FBST of the measurements after the (regularised) projection of each interferer's Fourier
@@ -13,7 +13,7 @@ oracle's cross Gram matrices or its normal-equation solves:
   bhat_p = delta F_u A_p^{-2} w_p for a single interferer;
 * no interferers: the plain FBST;
 * physics: an interferer on a grid beam is removed from every beam, and a source far from it
-  passes almost unchanged (the interference bias of Sec. VI-B is small when the two are apart).
+  passes almost unchanged (the interference bias of Sec. VIII-B is small when the two are apart).
 """
 import numpy as np
 import pytest
