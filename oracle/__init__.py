@@ -6,7 +6,8 @@ leg of bench.py. The CUDA library and its Python binding never import it.
 Parity status of each function is stated in fbst_oracle's docstrings; every function is pinned by
 the tests in tests/test_oracle_pins.py except the size of the noise-free bias of a plane wave,
 which the paper gives no number for ("parity unpinned": only a sanity bound is checked). The
-beamspace interference nulling of Eq. (14) is pinned by tests/test_oracle_nulling.py.
+beamspace interference nulling of Eq. (14) is pinned by tests/test_oracle_nulling.py, and the
+non-uniform arrays of Sec. IX (make_problem(..., offsets=...)) by tests/test_oracle_nonuniform.py.
 """
 from .fbst_oracle import (  # noqa: F401
     Problem,

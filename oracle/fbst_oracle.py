@@ -95,9 +95,11 @@ class Problem:
 
 def make_problem(kind: str, mx: int, my: int, bx: int, by: int, N: int, frac_bw: float,
                  epsilon: float = 1.01, gamma: float = 2.0, delta: float | None = None,
-                 delta_rel: float | None = None, L: int | None = None) -> Problem:
-    """Build a Problem. L = gamma*N unless given. delta is absolute, or delta_rel*M*N."""
-    geom = ArrayGeometry(kind, mx, my)
+                 delta_rel: float | None = None, L: int | None = None, offsets=None) -> Problem:
+    """Build a Problem. L = gamma*N unless given. delta is absolute, or delta_rel*M*N. `offsets`
+    (M pairs, half wavelengths) moves the elements off the grid: a non-uniform array (Sec. IX),
+    for which every sum below is the same direct sum over the actual positions."""
+    geom = ArrayGeometry(kind, mx, my, None if offsets is None else tuple(map(tuple, offsets)))
     if L is None:
         L = int(round(gamma * N))
     if delta is None:

@@ -15,4 +15,5 @@ from .planewave import (  # noqa: F401
     ura_config,
     uneven_ula_instances,
     interference_config,
+    perturbed_geometry,
 )

@@ -30,11 +30,13 @@ import numpy as np
 
 @dataclass(frozen=True)
 class ArrayGeometry:
-    """A uniform linear array ("ula", mx elements) or an mx-by-my uniform rectangular array."""
+    """A linear array ("ula", mx elements) or an mx-by-my rectangular array on the half-wavelength
+    grid, optionally moved off it by per-element offsets (a non-uniform array, Sec. IX)."""
 
     kind: str
     mx: int
     my: int = 1
+    offsets: tuple | None = None  # M pairs (dx, dy), half wavelengths, added to the grid positions
 
     @property
     def M(self) -> int:
@@ -50,11 +52,27 @@ def array_positions(geom: ArrayGeometry) -> np.ndarray:
     if geom.kind == "ula":
         if geom.my != 1:
             raise ValueError("a linear array has my == 1")
-        return np.stack([np.arange(geom.mx, dtype=np.float64), np.zeros(geom.mx)], axis=1)
-    if geom.kind == "ura":
+        pos = np.stack([np.arange(geom.mx, dtype=np.float64), np.zeros(geom.mx)], axis=1)
+    elif geom.kind == "ura":
         kx, ky = np.meshgrid(np.arange(geom.mx), np.arange(geom.my), indexing="ij")
-        return np.stack([kx.ravel(), ky.ravel()], axis=1).astype(np.float64)
-    raise ValueError(f"unknown array kind {geom.kind!r}")
+        pos = np.stack([kx.ravel(), ky.ravel()], axis=1).astype(np.float64)
+    else:
+        raise ValueError(f"unknown array kind {geom.kind!r}")
+    if geom.offsets is not None:
+        pos = pos + np.asarray(geom.offsets, dtype=np.float64).reshape(geom.M, 2)
+    return pos
+
+
+def perturbed_geometry(kind: str, mx: int, my: int, sigma: float, seed: int) -> ArrayGeometry:
+    """Grid positions moved by independent N(0, sigma^2) offsets in half wavelengths (along x only for
+    a linear array), element 0 kept at the origin as the phase reference: non-uniform spacing
+    emulated from a uniform array, as the experiments of Sec. IX do."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    off = rng.normal(0.0, sigma, (mx * my, 2))
+    if kind == "ula":
+        off[:, 1] = 0.0
+    off[0] = 0.0
+    return ArrayGeometry(kind, mx, my, tuple(map(tuple, off.tolist())))
 
 
 @dataclass
