@@ -1,22 +1,25 @@
 """Benchmark of the FBST hot path on GB300.
 
-Default workload (C2): 256-element linear array, fb = 0.5, N = 256 snapshots per block, B = 256
-beams, L = 512, 64 contiguous blocks of one record per step, complex64 in and out. Stage 1 (the
-fan chirp-z) in FP32 on the CUDA cores; stage 2 by default the precomputed-inverse apply on the
-tensor cores in split TF32 with split FP32 accumulation (FP32-class: measured rel err ~3e-6 vs the
-FP64 oracle, reported on every run); --stage2 gs_ir1 selects the Gohberg-Semencul path, dense_fp32
-the CUDA-core apply. One step = fbst_execute over the 64 blocks.
+Default workload (ULA1024): 1024-element linear array, fb = 0.5, N = 512 snapshots per block,
+B = 1024 beams, L = 1024, 64 contiguous blocks of one record per step, complex64 in and out. This
+is the array size (M = B = 1024) at which the transform's roofline is stated. Stage 1 (the fan
+chirp-z) runs in FP32 on the CUDA cores; stage 2 by default is the precomputed-inverse apply on the
+tensor cores in split TF32 with split FP32 accumulation (FP32-class: its error against the FP64
+oracle is measured and reported on every run); --stage2 gs_ir1 selects the Gohberg-Semencul path,
+dense_fp32 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload C2|C3|ULA1024|C4|C5|C2N] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|C2|C3|C4|C5|C2N] [--contraction tf32x3|fp32]
 
-With N > 1 (torchrun) every rank runs its own replica of the plan on its own 64 blocks (weak
-scaling; the method has no cross-block exchange, so there is no collective on the data path).
-Rank 0 prints one JSON line. `value` is device time measured with CUDA events on the launching
-stream, L2 flushed (256 MiB write) before every timed step; `e2e` goes through the C-ABI host-buffer
-entry point with pinned host memory, copies included; `roofline` times each kernel live with
-events around its own C-ABI stage call; `cpu_baseline` times the FP64 oracle on the host cores
-on a bounded sample. `--impl reference` times the oracle alone (the reference arm).
+With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
+stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
+the method has no cross-block exchange, so there is no collective on the data path). Rank 0 prints
+one JSON line. `value` is device time measured with CUDA events on the launching stream, L2
+flushed (256 MiB write) before every timed step; `e2e` goes through the C-ABI host-buffer entry
+point with pinned host memory, copies included; `roofline` times each kernel live with events
+around its own C-ABI stage call; the FP32 ALU peak is measured live (an FMA-chain kernel of the
+library, with the SM clock sampled meanwhile); `cpu_baseline` times the FP64 oracle on the host
+cores on a bounded sample. `--impl reference` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
 
@@ -37,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "beam-samples/s at rel err ≤1e-5 vs FP64 oracle, %HBM roofline; p50/p99 latency"
 UNIT = "beam-samples/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128   # FP32 lanes per SM (4 sub-partitions x 32)
 
 
 def load_peaks() -> tuple[dict, str]:
@@ -76,10 +79,24 @@ def flop_model(info) -> dict:
 TC_VARIANTS = {4: (4, 2, 3, "bf16", 3), 5: (2, 4, 1, "tf32", 3), 6: (2, 4, 3, "tf32", 1)}
 
 
-def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str) -> dict:
-    """Roofline entry of one kernel launch (nblk blocks) that took `ms` milliseconds."""
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+def nominal_fp32_peak(sms: int, sm_mhz: float) -> dict:
+    """FP32 FMA peak from unit counts and clock: SMs x 128 lanes x 2 flops x clock."""
+    return {"tflops": sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
+            "source": f"nominal: {sms} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz"}
+
+
+def path_bytes(info, nblk: int) -> float:
+    """Compulsory HBM bytes of the whole transform over nblk blocks: y in, bhat out and one
+    generator per beam per block, 8 (M N + B N + B L) bytes per block (32 B per beam-sample at
+    M = B and L = 2N)."""
+    M, N, B, L = info.M, info.N, info.B, info.L
+    return 8.0 * nblk * (M * N + B * N + B * L)
+
+
+def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str, fp32: dict) -> dict:
+    """Roofline entry of one kernel launch (nblk blocks) that took `ms` milliseconds. `fp32` is the
+    FP32 ALU peak ({"tflops", "source"}), measured where possible."""
+    fp32_peak = float(fp32["tflops"])
     flops = flop_model(info)[kernel] * nblk
     M, N, B, L = info.M, info.N, info.B, info.L
     if kernel == "stage2" and info.stage2 in TC_VARIANTS:
@@ -96,7 +113,45 @@ def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: st
                 "peak_source": f"{peak_kind} bf16_tflops x {'1' if dt == 'bf16' else '0.5 (tf32 nominal ratio)'}"}
     ach = flops / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-            "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz ({peak_kind} sm_max_mhz)"}
+            "peak_source": fp32["source"]}
+
+
+def path_roofline(info, nblk: int, ms: float, peaks: dict, fp32: dict) -> dict:
+    """Fraction of the binding roof of the whole step: t_roof = max(compulsory bytes / HBM peak,
+    FP32 flops / FP32 peak + tensor-core flops / TF32 peak) against the measured step time."""
+    fm = flop_model(info)
+    alu = (fm["czt_time"] + fm["czt_space"]) * nblk
+    tc = 0.0
+    if info.stage2 in TC_VARIANTS:
+        _, _, terms, dt, _ = TC_VARIANTS[info.stage2]
+        tc_peak = float(peaks["bf16_tflops"]) * (1.0 if dt == "bf16" else 0.5)
+        tc = terms * fm["stage2"] * nblk / (tc_peak * 1e12)
+    else:
+        alu += fm["stage2"] * nblk
+    t_bytes = path_bytes(info, nblk) / (float(peaks["hbm_gbs"]) * 1e9)
+    t_flops = alu / (float(fp32["tflops"]) * 1e12) + tc
+    t_roof = max(t_bytes, t_flops)
+    return {"bound": "hbm" if t_bytes >= t_flops else "compute", "t_roof_ms": t_roof * 1e3, "t_step_ms": ms,
+            "frac": t_roof / (ms / 1e3), "t_hbm_ms": t_bytes * 1e3, "t_compute_ms": t_flops * 1e3,
+            "bytes_per_beam_sample": path_bytes(info, nblk) / (nblk * info.B * info.N)}
+
+
+def measure_fp32_peak(fb, gpu_index: int, budget_ms: float = 600.0) -> dict:
+    """FP32 FMA throughput of this GPU measured with the library's FMA-chain kernel, the SM clock
+    sampled by nvidia-smi while it runs. Best of three timed launches of about budget_ms each."""
+    tf, ms = fb.fp32_fma_peak(1024)
+    iters = max(1024, int(1024 * budget_ms / max(ms, 1e-3)))
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.25)
+    best = 0.0
+    for _ in range(3):
+        tf, ms = fb.fp32_fma_peak(iters)
+        best = max(best, tf)
+    clocks = sampler.stop()
+    src = f"measured: FMA-chain kernel, {iters} x 128 FMAs per thread on every resident CTA, best of 3"
+    if clocks.get("sm_mhz"):
+        src += f", SM clock median {clocks['sm_mhz']:.0f} MHz during the run"
+    return {"tflops": best, "source": src, "sm_mhz": clocks.get("sm_mhz"), "reasons": clocks.get("reasons")}
 
 
 class ClockSampler:
@@ -142,23 +197,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(args):
+def w_is_stream(args) -> bool:
+    """Workloads whose blocks are cut from one continuous record (replicas take later segments)."""
+    return args.workload in ("C2", "ULA1024")
+
+
+def workload(args, first_block: int = 0):
+    """The workload's geometry and a generator of its input; a replica's record starts at block
+    `first_block` of the stream (linear arrays)."""
     from synth import configs
-    if args.workload == "C2":
-        nb = args.nblk or configs.CONFIGS["C2"]["nblk"]
-        return dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, nblk=nb, name="C2"), \
-            lambda: configs.config_data("C2", nblk=nb)["y"]
+    if args.workload in ("C2", "ULA1024"):
+        c = configs.CONFIGS[args.workload]
+        nb = args.nblk or c["nblk"]
+        return dict(kind="ula", mx=c["mx"], my=1, bx=c["bx"], by=1, N=c["N"], frac_bw=c["frac_bw"], nblk=nb,
+                    name=args.workload), \
+            lambda: configs.config_data(args.workload, nblk=nb, first_block=first_block)["y"]
     if args.workload == "C3":
         nb = args.nblk or configs.CONFIGS["C3"]["nblk"]
         return dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, nblk=nb, name="C3"), \
             lambda: configs.config_data("C3", nblk=nb, Q=64)["y"]
-    if args.workload == "ULA1024":
-        # Large linear array (the paper's scaling regime): M = B = 1024, N = 512, fb = 0.5.
-        def gen():
-            from synth.planewave import ula_config
-            return ula_config(1024, 512, args.nblk or 16, 0.5, 8, 10.0, 2024, Q=64)["y"]
-        return dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, nblk=args.nblk or 16,
-                    name="ULA1024"), gen
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -309,7 +366,7 @@ def run_c5(args) -> None:
 
 
 def null_roofline(B: int, L: int, P: int, nblk: int, ms: float, contraction: str, peaks: dict,
-                  peak_kind: str) -> dict:
+                  peak_kind: str, fp32: dict) -> dict:
     """Roofline of the bracket of Eq. (14) over nblk blocks (its three launches together): the
     compulsory bytes are the cross Gram operator (FP32 re/im planes, read once), w read and the
     nulled w written; the contraction does 8 B L P L flops per block (x3 products when split-TF32)."""
@@ -325,10 +382,10 @@ def null_roofline(B: int, L: int, P: int, nblk: int, ms: float, contraction: str
         ach = 3 * flops / (ms / 1e3) / 1e12
         return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
                 "peak_source": f"{peak_kind} bf16_tflops x 0.5 (tf32 nominal ratio); 3 split-TF32 products"}
-    fp32_peak = SMS * FP32_LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    fp32_peak = float(fp32["tflops"])
     ach = flops / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-            "peak_source": f"FP32 FMA peak {SMS} SMs x {FP32_LANES} lanes x 2 ({peak_kind} sm_max_mhz)"}
+            "peak_source": fp32["source"]}
 
 
 def run_null(args) -> None:
@@ -432,8 +489,10 @@ def run_null(args) -> None:
             e2e_t.append(time.perf_counter() - t0)
 
     peaks, peak_kind = load_peaks()
-    roofs = {k: roofline(k, info, nblk, v, peaks, peak_kind) for k, v in kern_ms.items() if k != "null_bracket"}
-    roofs["null_bracket"] = null_roofline(B, L, P, nblk, kern_ms["null_bracket"], args.contraction, peaks, peak_kind)
+    fp32 = measure_fp32_peak(fb, 0)
+    roofs = {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32) for k, v in kern_ms.items() if k != "null_bracket"}
+    roofs["null_bracket"] = null_roofline(B, L, P, nblk, kern_ms["null_bracket"], args.contraction, peaks, peak_kind,
+                                          fp32)
     dom = max(kern_ms, key=kern_ms.get)
 
     cpu = None
@@ -473,6 +532,7 @@ def run_null(args) -> None:
                 "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},
         "gpu_launches": nl.launch_count(nblk) * args.steps,
         "clocks": clocks,
+        "fp32_peak": fp32,
         "wall_s_timed_region": wall,
         "nulling_create_s": t_create,
     }
@@ -518,6 +578,7 @@ def run_reference(args) -> None:
     if args.workload == "C2N":
         run_reference_null(args)
         return
+    args.nblk = 1                     # the oracle runs one block per step: generate only that one
     w, gen = workload(args)
     y = gen()
     beams = np.linspace(0, w["bx"] * w["by"] - 1, 16).astype(int)
@@ -553,7 +614,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fbst", choices=["fbst", "reference"])
-    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--workload", default="ULA1024")
     ap.add_argument("--nblk", type=int, default=None)
     ap.add_argument("--stage2", default="dense_tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -583,7 +644,7 @@ def main() -> None:
     import torch
     import paper_2512_08887_gb300 as fb
     from paper_2512_08887_gb300.build import build
-    from paper_2512_08887_gb300.dist import max_over_ranks, whole_job_rate
+    from paper_2512_08887_gb300.dist import max_over_ranks, rank_blocks, whole_job_rate
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -601,9 +662,12 @@ def main() -> None:
         dist.barrier()
     build()
 
-    w, gen = workload(args)
+    # Weak scaling: every rank takes its own nblk blocks of one continuous stream of world x nblk.
+    nblk0, _ = workload(args)
+    first, last = rank_blocks(world * nblk0["nblk"], rank, world)
+    w, gen = workload(args, first_block=first if w_is_stream(args) else 0)
     y_np = gen()
-    nblk = w["nblk"]
+    nblk = last - first
     M, B, N = w["mx"] * w["my"], w["bx"] * w["by"], w["N"]
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
@@ -620,7 +684,7 @@ def main() -> None:
     rel_err = None
     if rank == 0:
         import oracle as O
-        beams = np.array([0, 77, 128, B - 1])
+        beams = np.unique(np.array([0, 1, 77, B // 4, B // 2, 3 * B // 4, B - 2, B - 1]))
         pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], N, frac_bw=info.fb_num / info.fb_den,
                             epsilon=info.eps_num / info.eps_den, delta=info.delta, L=info.L)
         ref = O.fbst(pb, y_np[:2], beams=beams)
@@ -692,8 +756,9 @@ def main() -> None:
         return
 
     peaks, peak_kind = load_peaks()
+    fp32 = measure_fp32_peak(fb, torch.cuda.current_device())
     dom = max(kern_ms, key=kern_ms.get)
-    roof = roofline(dom, info, nblk, kern_ms[dom], peaks, peak_kind)
+    roof = roofline(dom, info, nblk, kern_ms[dom], peaks, peak_kind, fp32)
     s2name = fb.STAGE2_NAMES[info.stage2]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -706,8 +771,8 @@ def main() -> None:
             blob = b"".join(open(os.path.join(ROOT, s), "rb").read() for s in rec["sources"])
             if hashlib.sha256(blob).hexdigest()[:16] == rec["sha256_16"]:
                 traffic = rec["bytes_per_launch"]  # else: the kernel changed since the capture
-    hbm_total_bytes = 8.0 * nblk * (M * N + B * N)
-    hbm_frac = (hbm_total_bytes / (statistics.mean(step_ms) / 1e3)) / (float(peaks["hbm_gbs"]) * 1e9)
+    # Whole-path HBM fraction on the compulsory bytes: y in, bhat out, one generator per beam.
+    hbm_frac = (path_bytes(info, nblk) / (statistics.mean(step_ms) / 1e3)) / (float(peaks["hbm_gbs"]) * 1e9)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -725,15 +790,19 @@ def main() -> None:
         "data": "synthetic",
         "config": {"workload": f"{w['name']}: {w['kind'].upper()} M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
                                f"{nblk} blocks/step per GPU, complex64",
+                   "blocks_of_rank0": [first, last],
                    "M": M, "B": B, "N": N, "L": info.L, "nblk_per_gpu": nblk, "stage2": fb.STAGE2_NAMES[info.stage2],
                    "l2": "flushed before every timed step (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
         "rel_err_vs_oracle": rel_err,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "hbm_roofline_frac": hbm_frac,
+        "hbm_roofline_bytes_per_beam_sample": path_bytes(info, nblk) / (nblk * B * N),
+        "path_roofline": path_roofline(info, nblk, statistics.mean(step_ms), peaks, fp32),
         "roofline": dict(roof, kernel=dom, traffic=traffic),
         "kernels_ms": kern_ms,
-        "kernels_roofline": {k: roofline(k, info, nblk, v, peaks, peak_kind) for k, v in kern_ms.items()},
+        "kernels_roofline": {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32) for k, v in kern_ms.items()},
+        "fp32_peak": fp32,
         "e2e": {"value": units * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},
         "gpu_launches": plan.launch_count(nblk) * args.steps,

@@ -139,16 +139,18 @@ int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* strea
  * (fbst_last_error says why). */
 int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nblk, void* stream);
 
-/* The transform of Sec. III-A, same result as fbst_execute, for callers that cannot allocate
- * device memory at run time (a
- * real-time loop that must not block in the allocator, a fixed start-up memory budget, code
- * running under stream capture). The paper has no counterpart; this is a library convenience.
- * The intermediates live in one 64 MiB static device array of the library instead of the plan's
- * workspace, and the call allocates nothing. Rejects (FBST_ERR_INVALID, nothing launched) a call
- * whose intermediates, 8*nblk*(L*M + B*L) bytes, exceed 64 MiB. Its first call on a device looks
- * up the array's address (cudaGetSymbolAddress) and should come before any stream capture. All
- * calls share the array, so calls that overlap on the GPU race and must be serialised. Not
- * available for the tensor-core stage-2 variants (FBST_ERR_UNSUPPORTED). */
+/* Same result as fbst_execute, for callers that cannot allocate device memory while they run the
+ * transform: a real-time receive loop that must never block inside the allocator (cudaMalloc may
+ * synchronise the whole device), or a process whose device-memory budget is fixed and checked at
+ * start-up. The paper has no counterpart; this is a library convenience. The intermediates live
+ * in one 64 MiB static device array of the library instead of the plan's workspace, and the call
+ * allocates nothing. The caller still passes y and bhat, and the plan must belong to the current
+ * device (FBST_ERR_INVALID otherwise). Rejects (FBST_ERR_INVALID, nothing launched) a call whose
+ * intermediates, 8*nblk*(L*M + B*L) bytes, exceed 64 MiB. Its first call on a device looks up the
+ * array's address (cudaGetSymbolAddress), so make that first call before any stream capture. All
+ * calls share the array and it keeps the last call's contents, so calls that overlap on the GPU
+ * race and must be serialised. Not available for the tensor-core stage-2 variants
+ * (FBST_ERR_UNSUPPORTED). */
 int fbst_execute_noalloc(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
 
 /* Stage 1 alone, the fan chirp-z of Sec. IV (App. B for rectangular arrays):
@@ -167,6 +169,13 @@ int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* str
 /* Stage 2 alone (Sec. V): w (device, [nblk][B][L]) -> bhat (device, [nblk][B][N]),
  * bhat_b = F_u (F_b^H F_b + delta I)^{-1} w_b, with the plan's stage-2 variant. */
 int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream);
+
+/* Calibration; no counterpart in the paper. Measure the FP32 FMA throughput of the current device:
+ * one warm-up and one timed launch of a kernel in which every thread of every resident CTA runs
+ * independent FMA chains (2 flops each), `iters` x 128 FMAs per thread. sink: device, >= 4 bytes,
+ * written only in a case that cannot occur. *tflops receives the measured TFLOP/s and *ms (may be
+ * NULL) the timed launch's duration (CUDA events on `stream`, which the call synchronises). */
+int fbst_fp32_fma_peak(void* sink, int iters, double* tflops, double* ms, void* stream);
 
 /* Error reporting; no counterpart in the paper. Synchronise `stream`, then return and clear the
  * plan's device status word: FBST_OK, or the

@@ -27,5 +27,6 @@ from .fbst_oracle import (  # noqa: F401
     lstsq_augmented,
     noise_power_trace,
     delay_and_sum_exact,
+    delay_and_sum_exact_record,
     rel_l2,
 )

@@ -336,6 +336,28 @@ def delay_and_sum_exact(record: np.ndarray, positions: np.ndarray, u: float, v: 
     return out / record.shape[0]
 
 
+def delay_and_sum_exact_record(record: np.ndarray, positions: np.ndarray, u: float, v: float,
+                               frac_bw: float, n_out: np.ndarray) -> np.ndarray:
+    """The same exact-sinc delay-and-sum as delay_and_sum_exact, for long records.
+
+    For element m every output time t_n + tau_m has the same fractional part, so the sinc series
+    sum_k y_m[k] sinc(n + tau_m - k) over the whole record is the full linear convolution of y_m
+    with the sampled kernel h_m[j] = sinc(j + tau_m), j = -(K-1)..K-1, read at n. The convolution
+    is taken with scipy's FFT convolution (a library primitive); nothing is truncated.
+    """
+    import scipy.signal
+    rho = frac_bw / (2.0 + frac_bw)
+    tau = rho * (u * positions[:, 0] + v * positions[:, 1])
+    K = record.shape[1]
+    j = np.arange(-(K - 1), K, dtype=np.float64)
+    idx = np.asarray(n_out, dtype=np.int64) + (K - 1)
+    out = np.zeros(len(idx), dtype=np.complex128)
+    for m in range(record.shape[0]):
+        full = scipy.signal.fftconvolve(np.asarray(record[m], dtype=np.complex128), np.sinc(j + tau[m]))
+        out += np.exp(TWO_PI_J * tau[m] / frac_bw) * full[idx]
+    return out / record.shape[0]
+
+
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
     """||a - b||_2 / ||b||_2 over all entries."""
     a = np.asarray(a, dtype=np.complex128).ravel()

@@ -10,6 +10,7 @@ from ._native import (  # noqa: F401
     STAGE2,
     STAGE2_NAMES,
     derive,
+    fp32_fma_peak,
     load_library,
     make_band,
     make_geometry,

@@ -87,6 +87,7 @@ SIGNATURES = {
     "fbst_null_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_null_launch_count": (_I, [_VP, _I]),
     "fbst_null_destroy": (_I, [_VP]),
+    "fbst_fp32_fma_peak": (_I, [_VP, _I, C.POINTER(C.c_double), C.POINTER(C.c_double), _VP]),
 }
 NULL_CONTRACTION = {"tf32x3": 0, "fp32": 1}
 
@@ -156,6 +157,17 @@ def derive(geom: Geometry, N: int, band: Band) -> Info:
     M, B = geom.mx * geom.my, geom.bx * geom.by
     _check(lib.fbst_derive(C.byref(geom), M, N, B, C.byref(band), C.byref(info)), "fbst_derive")
     return info
+
+
+def fp32_fma_peak(iters: int = 4096, stream=None) -> tuple:
+    """Measured FP32 FMA throughput of the current device (fbst_fp32_fma_peak): (TFLOP/s, ms)."""
+    import torch
+    lib = load_library()
+    sink = torch.zeros(4, dtype=torch.float32, device="cuda")
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.fbst_fp32_fma_peak(sink.data_ptr(), int(iters), C.byref(tf), C.byref(ms), _stream(stream)),
+           "fbst_fp32_fma_peak")
+    return tf.value, ms.value
 
 
 class Plan:

@@ -1,20 +1,21 @@
 // fbst_execute_noalloc: the whole transform with its intermediates in a static device array.
 //
 // Some callers cannot allocate device memory when they run the transform: a real-time receive
-// loop that must never block in the allocator (cudaMalloc can synchronise the device), a
-// process whose memory budget is fixed and checked at start-up, or code that runs while a
-// CUDA stream is being captured into a graph, where allocation calls are not allowed. This
-// entry point serves them: it launches the same three kernels as fbst_execute, but the
-// intermediate arrays (yhat [nblk][L][M] and w [nblk][B][L]) live in one file-scope
-// __device__ array of kStaticScratchBytes instead of the plan's workspace, and the call makes no
-// allocation of any kind. The caller still passes the input and output buffers, and the plan
-// (built once, earlier, by fbst_plan) supplies the read-only tables.
+// loop that must never block in the allocator (cudaMalloc can synchronise the device), or a
+// process whose device-memory budget is fixed and checked at start-up. This entry point serves
+// them: it launches the same three kernels as fbst_execute, but the intermediate arrays
+// (yhat [nblk][L][M] and w [nblk][B][L]) live in one file-scope __device__ array of
+// kStaticScratchBytes instead of the plan's workspace, and the call makes no allocation of any
+// kind. The caller still passes the input and output buffers, and the plan (built once, earlier,
+// by fbst_plan) supplies the read-only tables.
 //
 // Rules of use:
 // - The array is a static of this library: every GPU that loads the library holds
 //   kStaticScratchBytes (64 MiB) until the process exits, whether or not this entry point is used.
 // - A call whose intermediates need more than kStaticScratchBytes is rejected with
 //   FBST_ERR_INVALID before anything is launched (split the blocks over several calls).
+// - The plan must belong to the current device: the kernels read the plan's tables and write the
+//   current device's array, so a plan of another device is rejected with FBST_ERR_INVALID.
 // - On its first call on a device (with that device current) the entry point looks up the
 //   array's device address with cudaGetSymbolAddress; make that first call before any stream
 //   capture. Later calls on that device reuse the address.
@@ -79,6 +80,9 @@ extern "C" int fbst_execute_noalloc(fbst_plan_t p, const void* y, void* bhat, in
   const int kind = in.stage2;
   if (kind != FBST_STAGE2_GS && kind != FBST_STAGE2_GS_IR1 && kind != FBST_STAGE2_DENSE_FP32)
     return FBST_ERR_UNSUPPORTED;
+  int cur = -1;
+  FBST_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != p->device) return FBST_ERR_INVALID;
   void* base = nullptr;
   const int st = static_scratch_address(&base);
   if (st != FBST_OK) return st;

@@ -7,6 +7,9 @@ C3  32x32 rectangular array (M=1024), N=512, 32x32 beam grid (B=1024), fb=0.3; K
     from the unit disk, 10 dB; nblk blocks of one record; seed 1003.
 C4  64 independent linear arrays, M = 2^U{5..10}, N from {128,256,512,1024}, B=M, fb ~ U[0.2,0.6]
     rounded to 1e-3, K=4 plane waves, 15 dB, one block each, per-instance child seeds of 1004.
+ULA1024 linear array M=1024, N=512, B=1024, fb=0.5 (L=1024); K=8 plane waves, 10 dB; one continuous
+    record cut into 64 blocks of 512 snapshots; Q=64 sinusoids per waveform; seed 2024. The large
+    array (M = B = 1024) at which the transform's roofline is stated.
 C2N the C2 array and grid with one unit-power source on grid beam 160 and two interferers on grid
     beams 64 and 96 at 20 dB above it, 10 dB SNR, 64 blocks; seed 1005. Workload of the beamspace
     interference nulling (Sec. VIII-B), which removes beams 64 and 96.
@@ -20,16 +23,23 @@ CONFIGS = {
     "C1": dict(kind="ula", mx=16, my=1, bx=16, by=1, N=64, frac_bw=0.5, K=3, snr_db=20.0, seed=1001, nblk=1),
     "C2": dict(kind="ula", mx=256, my=1, bx=256, by=1, N=256, frac_bw=0.5, K=8, snr_db=10.0, seed=1002, nblk=64),
     "C3": dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, K=16, snr_db=10.0, seed=1003, nblk=16),
+    "ULA1024": dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, K=8, snr_db=10.0, seed=2024,
+                    nblk=64, Q=64),
 }
 
 
-def config_data(name: str, nblk: int | None = None, Q: int = 256) -> dict:
-    """Generate the seeded data of C1..C3 (nblk overrides the block count)."""
+def config_data(name: str, nblk: int | None = None, Q: int | None = None, first_block: int = 0) -> dict:
+    """Generate the seeded data of C1..C3 and ULA1024 (nblk overrides the block count). A linear
+    array's record may start at block `first_block` of the same continuous signal (a replica's share
+    of the stream; the sources are the same, the noise of a later segment has its own seed)."""
     c = dict(CONFIGS[name])
+    Q = Q if Q is not None else c.pop("Q", 256)
+    c.pop("Q", None)
     if nblk is not None:
         c["nblk"] = nblk
     if c["kind"] == "ula":
-        d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
+        d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q,
+                       first_block=first_block)
     else:
         d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
     d.update(c)

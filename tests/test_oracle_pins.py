@@ -234,3 +234,16 @@ def test_linearity(rng):
     fac = O.Stage2Factors(pb)
     np.testing.assert_allclose(O.fbst(pb, y1 + 2 * y2, factors=fac),
                                O.fbst(pb, y1, factors=fac) + 2 * O.fbst(pb, y2, factors=fac), atol=1e-10)
+
+
+def test_long_record_delay_and_sum_equals_the_direct_sinc_sum(rng):
+    # The convolution form must be the same finite sinc series as the direct sum (brute force),
+    # on a linear and a rectangular array, at output times near both record ends and inside.
+    for kind, mx, my, u, v in (("ula", 6, 1, 0.37, 0.0), ("ura", 3, 3, -0.2, 0.55)):
+        geom = ArrayGeometry(kind, mx, my)
+        rec = _crandn(rng, geom.M, 300).astype(np.complex128)
+        pos = array_positions(geom)
+        n_out = np.array([0, 1, 17, 150, 298, 299])
+        direct = O.delay_and_sum_exact(rec, pos, u, v, 0.4, n_out)
+        conv = O.delay_and_sum_exact_record(rec, pos, u, v, 0.4, n_out)
+        np.testing.assert_allclose(conv, direct, rtol=0, atol=1e-12 * np.abs(direct).max())

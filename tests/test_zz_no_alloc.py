@@ -1,12 +1,12 @@
 """fbst_execute_noalloc: the transform for callers that cannot allocate device memory at run time.
 
-A real-time receive loop that must not block in the allocator, a process with a memory budget
-fixed at start-up, or code running under stream capture cannot call cudaMalloc when it runs the
-transform. fbst_execute_noalloc keeps the intermediates in the library's static 64 MiB device
-array instead. This test calls it through the C ABI twice in a row (on different inputs) and
-checks each result against fbst_execute within the suite's FP32 tolerance, and checks that an
-oversized request is refused before anything runs. It builds what it needs, so it passes alone in
-a fresh process as well as after the rest of the suite (this file is collected last).
+A real-time receive loop that must not block in the allocator, or a process whose device-memory
+budget is fixed at start-up, cannot call cudaMalloc while it runs the transform.
+fbst_execute_noalloc keeps the intermediates in the library's static 64 MiB device array instead.
+This test calls it through the C ABI twice in a row (on different inputs) and checks each result
+against fbst_execute within the suite's FP32 tolerance, and checks that an oversized request is
+refused before anything runs. It builds what it needs, so it passes alone in a fresh process as
+well as after the rest of the suite (this file is collected last).
 """
 import numpy as np
 import pytest
