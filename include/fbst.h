@@ -105,7 +105,8 @@ typedef struct {
   double gamma_bound;    /* right-hand side of Eq. (4) */
   int warn_snapshots;    /* 1 if N does not exceed the Eq. (8) bound */
   int warn_gamma;        /* 1 if gamma does not exceed the Eq. (4) bound */
-  size_t table_bytes;     /* device bytes of the plan's tables */
+  size_t table_bytes;     /* device bytes of the plan's tables, held for its lifetime (the plan-time
+                             temporaries come and go during fbst_plan) */
   size_t workspace_bytes; /* device bytes of the plan's per-call workspace */
 } fbst_info;
 
@@ -116,13 +117,28 @@ typedef struct {
  * input and fills *out otherwise. */
 int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fbst_band* band, fbst_info* out);
 
+/* Device-memory allocator of a plan; no counterpart in the paper. alloc returns `bytes` of device
+ * memory of the plan's device, 16-byte aligned (256 recommended), usable in stream order on
+ * `stream`, or NULL when it has none; free takes back a block that alloc returned, with the same
+ * byte count, in stream order on `stream`. ctx is the caller's pointer, passed through. The
+ * library calls them only from inside its own entry points, on the calling host thread. */
+typedef void* (*fbst_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*fbst_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
 /* Build a plan on the current CUDA device: chirp tables and Bluestein kernel spectra (exact
  * integer reduction of the quadratic phases, FP64), Toeplitz generators of every A_b (Sec. V),
  * FP64 Levinson solves for the first column of A_b^{-1}, and either the Gohberg-Semencul spectra
  * or the dense operators G_b = F_u A_b^{-1}. Plan-time kernels run on `stream` and the call
- * synchronises it before returning. The plan owns all of its device memory. */
+ * synchronises it before returning.
+ * Memory: every device block the plan ever holds (its tables and workspace, plan-time
+ * temporaries, the staging buffers of fbst_execute_host, fbst_autotune's test input, and the
+ * memory of nulling objects built on it) comes from alloc(bytes, stream, ctx) and goes back
+ * through free(ptr, bytes, stream, ctx), both ordered on this `stream`, which must stay valid until
+ * fbst_destroy. alloc = free = NULL selects cudaMallocAsync / cudaFreeAsync on `stream`; giving
+ * only one of them is FBST_ERR_INVALID. When alloc returns NULL the call fails with FBST_ERR_OOM
+ * and everything it had obtained is freed again (nothing leaks). */
 int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band,
-              void* stream);
+              void* stream, fbst_alloc_fn alloc, fbst_free_fn free, void* ctx);
 
 /* Whole transform: y (device, [nblk][M][N]) -> bhat (device, [nblk][B][N]). nblk = 0 is a no-op.
  * Blocks are independent contiguous batches of N snapshots (Sec. III-A, streaming paragraph). */
@@ -170,6 +186,14 @@ int fbst_czt_space(fbst_plan_t p, const void* yhat, void* w, int nblk, void* str
  * bhat_b = F_u (F_b^H F_b + delta I)^{-1} w_b, with the plan's stage-2 variant. */
 int fbst_toeplitz_apply(fbst_plan_t p, const void* w, void* bhat, int nblk, void* stream);
 
+/* Failure detection; no counterpart in the paper. Set the limit, in nanoseconds, of each pipeline
+ * wait of the plan's tensor-core stage-2 kernels (and of the nulling contraction built on the
+ * plan) for later launches; 0 restores the default of 1 s. A wait that runs out makes the kernel
+ * record FBST_ERR_TIMEOUT in the plan's status word (read by fbst_sync_status), wait up to 2 s for
+ * its own copies and MMAs in flight, free its tensor memory and return; that launch's output is
+ * then not valid. A very small limit makes the next launch time out, which tests this path. */
+int fbst_set_wait_limit(fbst_plan_t p, uint64_t ns);
+
 /* Calibration; no counterpart in the paper. Measure the FP32 FMA throughput of the current device:
  * one warm-up and one timed launch of a kernel in which every thread of every resident CTA runs
  * independent FMA chains (2 flops each), `iters` x 128 FMAs per thread. sink: device, >= 4 bytes,
@@ -191,8 +215,11 @@ int fbst_plan_info(fbst_plan_t p, fbst_info* out);
  * memory `x_host` as [B][L] complex128 (interleaved doubles). Exposed for testing. */
 int fbst_plan_generators(fbst_plan_t p, void* x_host);
 
-/* Resource management; no counterpart in the paper. Free the plan and all of its device memory.
- * Waits for the plan's outstanding work. NULL is OK. */
+/* Resource management; no counterpart in the paper. Free the plan and all of its device memory
+ * (including that of nulling objects still built on it) through its free function, in stream order
+ * on the stream given to fbst_plan. Does not synchronise the device: work that uses the plan on
+ * other streams must have finished, or be ordered before the plan's stream, before this call.
+ * NULL is OK. */
 int fbst_destroy(fbst_plan_t p);
 
 /* Error reporting; no counterpart in the paper. Static human-readable name of a status code (the
@@ -284,8 +311,8 @@ typedef enum {
 /* Build the nulling of `P` interferer beams (1 <= P <= 16; distinct grid indices in [0, B), read
  * from the host array `interferers`) for plan `p`, on the current device; plan-time kernels run
  * on `stream`, which the call synchronises. The plan must outlive the nulling object, and the two
- * must not run concurrently (they share the plan's workspace and status word). Device memory:
- * 8*B*L*P*L bytes of operator (held once; twice during the call), 32*P*P_gs bytes of spectra,
+ * must not run concurrently (they share the plan's workspace and status word). Device memory,
+ * all obtained through the plan's allocator (see fbst_plan): 8*B*L*P*L bytes of operator (held once; twice during the call), 32*P*P_gs bytes of spectra,
  * 8*max_blocks*(P*L + B*L) bytes of workspace (8*max_blocks*(B*P*L + B*L) for FBST_NULL_FP32).
  * FBST_ERR_INVALID for bad arguments, FBST_ERR_UNSUPPORTED when P*L is not a multiple of 8 for the
  * tensor-core contraction or the exact phase reductions would leave 64-bit range, FBST_ERR_OOM /
@@ -309,7 +336,9 @@ int fbst_null_execute(fbst_null_t n, const void* y, void* bhat, int nblk, void* 
 int fbst_null_launch_count(fbst_null_t n, int nblk);
 
 /* Resource management; no counterpart in the paper. Free the nulling object's device memory
- * (not the plan). Waits for outstanding work. NULL is OK. */
+ * (not the plan) through the plan's free function, in stream order on the plan's stream. Does not
+ * synchronise the device: work that uses the object must have finished, or be ordered before the
+ * plan's stream, before this call. NULL is OK. */
 int fbst_null_destroy(fbst_null_t n);
 
 #ifdef __cplusplus

@@ -1,5 +1,6 @@
 """GB300 (sm_103a) fast broadband beamspace transform: CUDA library + thin Python binding."""
 from ._native import (  # noqa: F401
+    Allocator,
     FBSTError,
     Band,
     Batch,
@@ -14,4 +15,5 @@ from ._native import (  # noqa: F401
     load_library,
     make_band,
     make_geometry,
+    torch_allocator,
 )

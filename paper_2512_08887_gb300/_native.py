@@ -59,7 +59,7 @@ class Info(C.Structure):
 _VP, _I = C.c_void_p, C.c_int
 SIGNATURES = {
     "fbst_derive": (_I, [C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), C.POINTER(Info)]),
-    "fbst_plan": (_I, [C.POINTER(_VP), C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), _VP]),
+    "fbst_plan": (_I, [C.POINTER(_VP), C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), _VP, _VP, _VP, _VP]),
     "fbst_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_execute_host": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_execute_noalloc": (_I, [_VP, _VP, _VP, _I, _VP]),
@@ -88,6 +88,7 @@ SIGNATURES = {
     "fbst_null_launch_count": (_I, [_VP, _I]),
     "fbst_null_destroy": (_I, [_VP]),
     "fbst_fp32_fma_peak": (_I, [_VP, _I, C.POINTER(C.c_double), C.POINTER(C.c_double), _VP]),
+    "fbst_set_wait_limit": (_I, [_VP, C.c_uint64]),
 }
 NULL_CONTRACTION = {"tf32x3": 0, "fp32": 1}
 
@@ -113,7 +114,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
 def _check(status: int, what: str) -> None:
     if status != FBST_OK:
         lib = load_library()
-        detail = lib.fbst_last_error().decode() if status == -3 else ""
+        detail = lib.fbst_last_error().decode() if status in (-2, -3) else ""
         raise FBSTError(status, what, detail)
 
 
@@ -170,16 +171,76 @@ def fp32_fma_peak(iters: int = 4096, stream=None) -> tuple:
     return tf.value, ms.value
 
 
-class Plan:
-    """An FBST plan on the current CUDA device (fbst_plan / fbst_destroy)."""
+# fbst_alloc_fn / fbst_free_fn of include/fbst.h.
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
-    def __init__(self, geom: Geometry, N: int, band: Band, stream=None):
+
+class Allocator:
+    """A device allocator for fbst_plan: `alloc(nbytes, stream) -> address` (0 when it has no
+    memory) and `free(address, nbytes, stream)`, Python callables; `stream` is the cudaStream_t as an
+    integer. Holds the ctypes callbacks, which must live as long as any plan that uses them."""
+
+    def __init__(self, alloc, free):
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(alloc(int(nbytes), int(stream or 0))) or None
+            except Exception:                   # an allocator failure is FBST_ERR_OOM, not a crash
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            try:
+                free(int(ptr), int(nbytes), int(stream or 0))
+            except Exception:
+                pass
+
+        self.c_alloc, self.c_free = ALLOC_FN(_alloc), FREE_FN(_free)
+
+    def pointers(self) -> tuple:
+        return C.cast(self.c_alloc, C.c_void_p).value, C.cast(self.c_free, C.c_void_p).value
+
+
+_torch_allocator = None
+
+
+def torch_allocator() -> Allocator:
+    """PyTorch's caching allocator (torch.cuda.caching_allocator_alloc / _delete), stream-ordered
+    on the stream the plan was built on."""
+    global _torch_allocator
+    if _torch_allocator is None:
+        import torch
+
+        def alloc(nbytes, stream):
+            return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+        def free(ptr, nbytes, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        _torch_allocator = Allocator(alloc, free)
+    return _torch_allocator
+
+
+class Plan:
+    """An FBST plan on the current CUDA device (fbst_plan / fbst_destroy).
+
+    `allocator`: "torch" (default) takes the plan's device memory from PyTorch's caching
+    allocator; None lets the library use cudaMallocAsync; or an Allocator. Its memory is allocated
+    and freed in stream order on `stream` (default: the current stream), which must outlive the plan.
+    """
+
+    def __init__(self, geom: Geometry, N: int, band: Band, stream=None, allocator="torch"):
         self._lib = load_library()
         self.geom, self.band = geom, band
         self.M, self.B, self.N = geom.mx * geom.my, geom.bx * geom.by, N
+        if isinstance(allocator, str):
+            if allocator != "torch":
+                raise ValueError(f"unknown allocator {allocator!r}")
+            allocator = torch_allocator()
+        self._allocator = allocator                 # keeps the callbacks alive with the plan
+        fa, ff = allocator.pointers() if allocator is not None else (None, None)
         h = C.c_void_p()
         _check(self._lib.fbst_plan(C.byref(h), C.byref(geom), self.M, N, self.B, C.byref(band),
-                                   _stream(stream)), "fbst_plan")
+                                   _stream(stream), fa, ff, None), "fbst_plan")
         self._h = h
         self.info = Info()
         _check(self._lib.fbst_plan_info(self._h, C.byref(self.info)), "fbst_plan_info")
@@ -219,6 +280,10 @@ class Plan:
     def toeplitz_apply(self, w, bhat, nblk: int, stream=None) -> None:
         """Stage 2: w [nblk][B][L] -> bhat [nblk][B][N]."""
         self._call("fbst_toeplitz_apply", w, bhat, nblk, stream)
+
+    def set_wait_limit(self, ns: int) -> None:
+        """Limit of each pipeline wait of the tensor-core stage 2, ns (0 = default 1 s)."""
+        _check(self._lib.fbst_set_wait_limit(self._h, int(ns)), "fbst_set_wait_limit")
 
     def sync_status(self, stream=None) -> int:
         """Synchronise the stream; return and clear the plan's device status word (0 = OK)."""

@@ -1,8 +1,9 @@
-// C ABI of the FBST library (include/fbst.h): plan lifetime, execution and status reporting.
+// C ABI of the FBST library (include/fbst.h): plan lifetime, memory, execution and status reporting.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -14,29 +15,66 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", cudaGetErrorName(e), what, file, line);
 }
 
-template <typename T>
-static int dmalloc(T** ptr, size_t count) {
-  *ptr = nullptr;
-  if (count == 0) return FBST_OK;
-  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
-  if (e != cudaSuccess) {
-    *ptr = nullptr;
-    set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
-    cudaGetLastError();  // clear the sticky-free error state of a failed allocation
-    return e == cudaErrorMemoryAllocation ? FBST_ERR_OOM : FBST_ERR_CUDA;
+void set_last_error_message(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+struct mem_registry {
+  std::unordered_map<void*, size_t> live;   // block -> bytes
+};
+
+int plan_alloc(fbst_plan_s* p, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return FBST_OK;
+  if (!p->mem) return FBST_ERR_INVALID;
+  void* q = nullptr;
+  if (p->alloc_fn) {
+    q = p->alloc_fn(bytes, p->mem_stream, p->alloc_ctx);
+    if (!q) {
+      set_last_error_message("the plan's allocator returned NULL");
+      return FBST_ERR_OOM;
+    }
+    if (reinterpret_cast<uintptr_t>(q) & 15u) {
+      p->free_fn(q, bytes, p->mem_stream, p->alloc_ctx);
+      set_last_error_message("the plan's allocator returned a block that is not 16-byte aligned");
+      return FBST_ERR_INVALID;
+    }
+  } else {
+    const cudaError_t e = cudaMallocAsync(&q, bytes, p->mem_stream);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? FBST_ERR_OOM : FBST_ERR_CUDA;
+    }
   }
+  try {
+    p->mem->live.emplace(q, bytes);
+  } catch (...) {
+    if (p->free_fn) p->free_fn(q, bytes, p->mem_stream, p->alloc_ctx);
+    else cudaFreeAsync(q, p->mem_stream);
+    return FBST_ERR_OOM;
+  }
+  *out = q;
   return FBST_OK;
 }
 
+void plan_free(fbst_plan_s* p, void* q) {
+  if (!q || !p->mem) return;
+  auto it = p->mem->live.find(q);
+  if (it == p->mem->live.end()) return;
+  const size_t bytes = it->second;
+  p->mem->live.erase(it);
+  if (p->free_fn) p->free_fn(q, bytes, p->mem_stream, p->alloc_ctx);
+  else cudaFreeAsync(q, p->mem_stream);
+}
+
+// Every block still registered (the plan's own and those of nulling objects built on it).
 static void free_plan_memory(fbst_plan_s* p) {
-  void* ptrs[] = {p->tw32, p->tw64, p->pre_t, p->gspec_t, p->post_t,
-                  p->ax[0].pre, p->ax[0].kspec, p->ax[0].post,
-                  p->same_axes ? nullptr : p->ax[1].pre, p->same_axes ? nullptr : p->ax[1].kspec,
-                  p->same_axes ? nullptr : p->ax[1].post,
-                  p->XV, p->Aspec, p->pre_r, p->qspec_r, p->post_r, p->G, p->Gtc, p->x64,
-                  p->ws_yhat, p->ws_w, p->ws_tc, p->stage_y, p->stage_bhat, p->d_status};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  if (!p->mem) return;
+  while (!p->mem->live.empty()) plan_free(p, p->mem->live.begin()->first);
+}
+
+template <typename T>
+static int dmalloc(fbst_plan_s* p, T** ptr, size_t count) {
+  return plan_alloc_n(p, ptr, count);
 }
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
@@ -87,28 +125,39 @@ const char* fbst_status_string(int status) {
 
 const char* fbst_last_error(void) { return g_last_error; }
 
-int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band, void* stream) {
+int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band, void* stream,
+              fbst_alloc_fn alloc, fbst_free_fn free_fn, void* ctx) {
   if (!out) return FBST_ERR_INVALID;
   *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return FBST_ERR_INVALID;
   fbst_info info;
   FBST_TRY(fbst_derive(g, M, N, B, band, &info));
   if (g->kind == FBST_URA && info.P_space_x != info.P_space_y) return FBST_ERR_UNSUPPORTED;
   fbst_plan_s* p = new (std::nothrow) fbst_plan_s();
   if (!p) return FBST_ERR_OOM;
   std::memset(p, 0, sizeof(*p));
+  p->mem = new (std::nothrow) mem_registry();
+  if (!p->mem) {
+    delete p;
+    return FBST_ERR_OOM;
+  }
   p->info = info;
   p->geom = *g;
   p->band = *band;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  p->alloc_fn = alloc;
+  p->free_fn = free_fn;
+  p->alloc_ctx = ctx;
+  p->mem_stream = s;
   int r = FBST_OK;
   do {
     if (cudaGetDevice(&p->device) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     const int L = info.L;
-    if ((r = dmalloc(&p->tw32, kTwiddleSize)) != FBST_OK) break;
-    if ((r = dmalloc(&p->tw64, kTwiddleSize)) != FBST_OK) break;
-    if ((r = dmalloc(&p->pre_t, info.N)) != FBST_OK) break;
-    if ((r = dmalloc(&p->gspec_t, (size_t)info.S_time * info.P_time)) != FBST_OK) break;
-    if ((r = dmalloc(&p->post_t, L)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->tw32, kTwiddleSize)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->tw64, kTwiddleSize)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->pre_t, info.N)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->gspec_t, (size_t)info.S_time * info.P_time)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->post_t, L)) != FBST_OK) break;
     p->ax[0] = fbst_axis_tables{g->mx, g->bx, info.P_space_x, nullptr, nullptr, nullptr};
     p->n_axes = 1;
     p->same_axes = 1;
@@ -121,9 +170,9 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
     }
     for (int a = 0; a < p->n_axes && r == FBST_OK; ++a) {
       fbst_axis_tables& ax = p->ax[a];
-      if ((r = dmalloc(&ax.pre, (size_t)L * ax.Ma)) != FBST_OK) break;
-      if ((r = dmalloc(&ax.kspec, (size_t)L * ax.P)) != FBST_OK) break;
-      if ((r = dmalloc(&ax.post, (size_t)L * ax.Ba)) != FBST_OK) break;
+      if ((r = dmalloc(p, &ax.pre, (size_t)L * ax.Ma)) != FBST_OK) break;
+      if ((r = dmalloc(p, &ax.kspec, (size_t)L * ax.P)) != FBST_OK) break;
+      if ((r = dmalloc(p, &ax.post, (size_t)L * ax.Ba)) != FBST_OK) break;
     }
     if (r != FBST_OK) break;
     if (p->same_axes && g->kind == FBST_URA) {
@@ -131,25 +180,27 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
       p->ax[1].kspec = p->ax[0].kspec;
       p->ax[1].post = p->ax[0].post;
     }
-    if ((r = dmalloc(&p->x64, (size_t)B * L)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->x64, (size_t)B * L)) != FBST_OK) break;
     if (info.stage2 == FBST_STAGE2_GS || info.stage2 == FBST_STAGE2_GS_IR1) {
-      if ((r = dmalloc(&p->XV, (size_t)B * 2 * info.P_gs)) != FBST_OK) break;
-      if (info.stage2 == FBST_STAGE2_GS_IR1 && (r = dmalloc(&p->Aspec, (size_t)B * info.P_gs)) != FBST_OK) break;
-      if ((r = dmalloc(&p->pre_r, (size_t)L)) != FBST_OK) break;
-      if ((r = dmalloc(&p->qspec_r, (size_t)info.S_rec * info.P_rec)) != FBST_OK) break;
-      if ((r = dmalloc(&p->post_r, (size_t)info.N)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->XV, (size_t)B * 2 * info.P_gs)) != FBST_OK) break;
+      if (info.stage2 == FBST_STAGE2_GS_IR1 && (r = dmalloc(p, &p->Aspec, (size_t)B * info.P_gs)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->pre_r, (size_t)L)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->qspec_r, (size_t)info.S_rec * info.P_rec)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->post_r, (size_t)info.N)) != FBST_OK) break;
     } else {
-      if ((r = dmalloc(&p->G, (size_t)B * info.N * L)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->G, (size_t)B * info.N * L)) != FBST_OK) break;
     }
-    if ((r = dmalloc(&p->ws_yhat, (size_t)band->max_blocks * L * M)) != FBST_OK) break;
-    if ((r = dmalloc(&p->ws_w, (size_t)band->max_blocks * B * L)) != FBST_OK) break;
-    if ((r = dmalloc(&p->d_status, 1)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->ws_yhat, (size_t)band->max_blocks * L * M)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->ws_w, (size_t)band->max_blocks * B * L)) != FBST_OK) break;
+    if ((r = dmalloc(p, &p->d_status, 1)) != FBST_OK) break;
     if (cudaMemsetAsync(p->d_status, 0, sizeof(int), s) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     r = build_plan_tables(p, s);
   } while (0);
   if (r != FBST_OK) {
     cudaStreamSynchronize(s);
     free_plan_memory(p);
+    cudaStreamSynchronize(s);
+    delete p->mem;
     delete p;
     return r;
   }
@@ -159,12 +210,14 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
 
 int fbst_destroy(fbst_plan_t p) {
   if (!p) return FBST_OK;
-  cudaDeviceSynchronize();
+  // The host path's copy streams hold no pending work: fbst_execute_host synchronises before it
+  // returns. The frees are ordered on the plan's stream.
   for (cudaStream_t c : {p->copy_in, p->copy_out})
     if (c) cudaStreamDestroy(c);
   for (cudaEvent_t e : p->pipe_ev)
     if (e) cudaEventDestroy(e);
   free_plan_memory(p);
+  delete p->mem;
   delete p;
   return FBST_OK;
 }
@@ -177,6 +230,12 @@ int fbst_sync_status(fbst_plan_t p, void* stream) {
   FBST_CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) FBST_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
   return st;
+}
+
+int fbst_set_wait_limit(fbst_plan_t p, uint64_t ns) {
+  if (!p) return FBST_ERR_INVALID;
+  p->wait_ns = ns;
+  return FBST_OK;
 }
 
 int fbst_plan_info(fbst_plan_t p, fbst_info* out) {
@@ -338,8 +397,13 @@ int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nb
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const fbst_info& in = p->info;
   const int maxb = p->band.max_blocks;
-  if (!p->stage_y) FBST_TRY(dmalloc(&p->stage_y, (size_t)maxb * in.M * in.N));
-  if (!p->stage_bhat) FBST_TRY(dmalloc(&p->stage_bhat, (size_t)maxb * in.B * in.N));
+  if (!p->stage_y || !p->stage_bhat) {
+    if (!p->stage_y) FBST_TRY(dmalloc(p, &p->stage_y, (size_t)maxb * in.M * in.N));
+    if (!p->stage_bhat) FBST_TRY(dmalloc(p, &p->stage_bhat, (size_t)maxb * in.B * in.N));
+    // The staging blocks were allocated in stream order on the plan's stream; make them usable
+    // on the copy streams and `stream` (once).
+    FBST_CUDA_TRY(cudaStreamSynchronize(p->mem_stream));
+  }
   for (cudaStream_t* c : {&p->copy_in, &p->copy_out})
     if (!*c) FBST_CUDA_TRY(cudaStreamCreateWithFlags(c, cudaStreamNonBlocking));
   for (cudaEvent_t& e : p->pipe_ev)

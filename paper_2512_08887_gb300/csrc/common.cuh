@@ -102,11 +102,24 @@ struct fbst_axis_tables {
   float2* post;        // [L][Ba]   chirp postmultiply
 };
 
+namespace fbst {
+struct mem_registry;   // every live device block of a plan with its size (api.cu)
+}
+
 struct fbst_plan_s {
   fbst_info info;
   fbst_geometry geom;
   fbst_band band;
   int device;
+
+  // Device memory of the plan (tables, workspace, staging, temporaries, nulling objects) comes
+  // from the caller's allocator, or from cudaMallocAsync / cudaFreeAsync when none is given, and is
+  // always allocated and freed in stream order on mem_stream (the stream given to fbst_plan).
+  fbst_alloc_fn alloc_fn;
+  fbst_free_fn free_fn;
+  void* alloc_ctx;
+  cudaStream_t mem_stream;
+  fbst::mem_registry* mem;
 
   float2* tw32;        // [kTwiddleSize] twiddle ladder (see kTwiddleSize) rounded to float
   double2* tw64;       // same in double (plan-time FFTs)
@@ -152,6 +165,9 @@ struct fbst_plan_s {
   cudaEvent_t pipe_ev[12];
 
   int* d_status;       // device status word (FP64 plan kernels report here)
+  // Limit of one pipeline wait of the tensor-core stage-2 kernels, ns (0 = the default, 1 s);
+  // a wait that runs out makes the kernel record FBST_ERR_TIMEOUT, drain its copies and return.
+  unsigned long long wait_ns;
 
   // Launch shapes of the temporal and spatial chirp-z kernels ({0, 0} = built-in default;
   // fbst_autotune / fbst_set_shapes change them).
@@ -170,6 +186,28 @@ struct fbst_plan_s {
 
 namespace fbst {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void set_last_error_message(const char* msg);
+
+// Plan memory (api.cu). plan_alloc returns FBST_ERR_OOM when the allocator has no memory (and
+// FBST_ERR_INVALID for a block that is not 16-byte aligned); bytes = 0 gives a null pointer.
+// plan_free returns a block of this plan's registry (null and unknown pointers are ignored).
+int plan_alloc(fbst_plan_s* p, size_t bytes, void** out);
+void plan_free(fbst_plan_s* p, void* ptr);
+template <typename T>
+int plan_alloc_n(fbst_plan_s* p, T** out, size_t count) {
+  void* q = nullptr;
+  const int r = plan_alloc(p, count * sizeof(T), &q);
+  *out = static_cast<T*>(q);
+  return r;
+}
+// dst uses src's allocator and registry (a descriptor that shares the plan's memory accounting).
+inline void share_allocator(fbst_plan_s* dst, const fbst_plan_s* src) {
+  dst->alloc_fn = src->alloc_fn;
+  dst->free_fn = src->free_fn;
+  dst->alloc_ctx = src->alloc_ctx;
+  dst->mem_stream = src->mem_stream;
+  dst->mem = src->mem;
+}
 
 // Kernel launchers (each returns an fbst_status). All run on `s`.
 int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk, cudaStream_t s);

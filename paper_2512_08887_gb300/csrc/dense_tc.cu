@@ -67,7 +67,8 @@ static int variant_of(int stage2) {
 
 constexpr int kRowBytes = 128;    // one K-chunk row (the 128-byte swizzle span)
 constexpr int kTileM = 128;       // output samples per CTA (MMA M)
-constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait
+constexpr uint64_t kWaitNs = 1000000000ull;   // default limit of a pipeline wait (1 s; per plan)
+constexpr uint64_t kDrainNs = 2000000000ull;  // limit of the waits that drain copies / MMAs in flight
 
 // ---------------------------------------------------------------------------------------------
 // PTX helpers
@@ -100,12 +101,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false if it did not complete within kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false if it did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -252,7 +253,7 @@ struct tc_smem {
 template <int V, int NB>
 __global__ void __launch_bounds__(128, 1)
 k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-           float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status) {
+           float2* __restrict__ bhat, int B, int N, int L, int nblk, int* status, uint64_t wait_ns) {
   using TR = tc_traits<V>;
   using SM = tc_smem<V, NB>;
   constexpr int NPL = TR::NPL, STAGES = TR::STAGES;
@@ -302,7 +303,7 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     int issued = 0;
     for (int c = 0; c < nchunks; ++c) {
       const int s = c % STAGES;
-      if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) {
+      if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1, wait_ns)) {
         atomicExch(status, (int)FBST_ERR_TIMEOUT);
         *abort_flag = 1;
         break;
@@ -316,11 +317,10 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       }
       issued = c + 1;
     }
-    // Copies still in flight must land before the CTA can leave.
-    if (*abort_flag) {
-      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
-        (void)mbar_wait(&full[c % STAGES], (c / STAGES) & 1);
-    }
+    // Copies still in flight must land before the CTA can leave (on the normal path these phases
+    // have completed already and the waits return at once).
+    for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+      (void)mbar_wait(&full[c % STAGES], (c / STAGES) & 1, kDrainNs);
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t ID_POS = make_idesc(TR::FMT, kTileM, NB, false);
@@ -328,7 +328,7 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
       const int s = c % STAGES;
-      if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
+      if (!mbar_wait(&full[s], (c / STAGES) & 1, wait_ns)) {
         atomicExch(status, (int)FBST_ERR_TIMEOUT);
         *abort_flag = 1;
         ok = false;
@@ -368,9 +368,12 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   __syncwarp();
 
   // ---------------- Epilogue: all four warps ----------------
-  const bool have = mbar_wait(done, 0);
+  const bool have = mbar_wait(done, 0, wait_ns);
   if (!have) {
     if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
+    *abort_flag = 1;
+    // The MMAs already issued must finish before tensor memory is released.
+    (void)mbar_wait(done, 0, kDrainNs);
   } else if (!*abort_flag) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int n = m0 + warp * 32 + lane;
@@ -479,7 +482,7 @@ template <int NB, bool PERSIST>
 __global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int w_beam_mul,
-                 int* status) {
+                 int* status, uint64_t wait_ns) {
   using SM = fused_smem<NB>;
   constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
   constexpr int KELEM = kRowBytes / 4;  // 32 FP32 values of K per chunk
@@ -498,7 +501,8 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   uint64_t* afree = aready + KSTEPS;
   uint64_t* tfull = afree + KSTEPS;  // a tile's accumulators are complete
   uint64_t* tempty = tfull + 1;      // the epilogue has read them
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
+  uint64_t* mdone = tempty + 1;      // every MMA of this CTA has completed (before tensor memory is freed)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -529,6 +533,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, 128);
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -552,7 +557,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
       int m0, b, blk0;
       tile_of(ti, m0, b, blk0);
-      if (!mbar_wait(tfull, it & 1)) {
+      if (!mbar_wait(tfull, it & 1, wait_ns)) {
         if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
         *abort_flag = 1;
         break;
@@ -603,7 +608,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       tile_of(ti, m0, b, blk0);
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int s = gc % RS;
-        if ((gc >= RS && !mbar_wait(&rawfree[s], ((gc / RS) - 1) & 1)) || *abort_flag) {
+        if ((gc >= RS && !mbar_wait(&rawfree[s], ((gc / RS) - 1) & 1, wait_ns)) || *abort_flag) {
           ok = false;
           break;
         }
@@ -619,8 +624,10 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     if (!ok) {
       atomicExch(status, (int)FBST_ERR_TIMEOUT);
       *abort_flag = 1;
-      for (int g = (issued > RS ? issued - RS : 0); g < issued; ++g) (void)mbar_wait(&full[g % RS], (g / RS) & 1);
     }
+    // Copies still in flight must land before the CTA can leave (on the normal path these phases
+    // have completed already and the waits return at once).
+    for (int g = (issued > RS ? issued - RS : 0); g < issued; ++g) (void)mbar_wait(&full[g % RS], (g / RS) & 1, kDrainNs);
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t ID = make_idesc(2u, kTileM, 2 * NB, false);
@@ -628,14 +635,14 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     bool ok = true;
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
       // The accumulators of the previous tile must have been read out.
-      if (it >= 1 && !mbar_wait(tempty, (it - 1) & 1)) {
+      if (it >= 1 && !mbar_wait(tempty, (it - 1) & 1, wait_ns)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int c = 0; c < nchunks && ok; ++c, ++gc) {
         const int ps = gc % PS;
-        if (!mbar_wait(&wconv[ps], (gc / PS) & 1)) {
+        if (!mbar_wait(&wconv[ps], (gc / PS) & 1, wait_ns)) {
           ok = false;
           break;
         }
@@ -644,7 +651,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const uint32_t hacc = tmem + ((c & 1) ? H1 : H0), lacc = tmem + LO;
 #pragma unroll
         for (int k = 0; k < KSTEPS; ++k) {
-          if (!mbar_wait(&aready[k], gc & 1)) {
+          if (!mbar_wait(&aready[k], gc & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -669,9 +676,12 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     if (!ok) {
       atomicExch(status, (int)FBST_ERR_TIMEOUT);
       *abort_flag = 1;
-      // Let the MMAs already issued finish before tensor memory is released.
-      mma_commit(tfull);
+      mma_commit(tfull);   // releases an epilogue waiting for this tile (it then sees the abort flag)
     }
+    // Every MMA this thread issued must have finished before tensor memory is released, whether or
+    // not the epilogue read the last accumulators: a commit to a barrier of its own, waited for once.
+    mma_commit(mdone);
+    (void)mbar_wait(mdone, 0, kDrainNs);
   } else if (warp >= 4 && warp < 8) {
     // ---------------- converters ----------------
     const int ct = threadIdx.x - 128;  // A row and tensor-memory lane
@@ -681,7 +691,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int s = gc % RS, ps = gc % PS;
-        if (!mbar_wait(&full[s], (gc / RS) & 1) || *abort_flag) {
+        if (!mbar_wait(&full[s], (gc / RS) & 1, wait_ns) || *abort_flag) {
           ok = false;
           break;
         }
@@ -694,7 +704,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           ar[j] = *reinterpret_cast<const float4*>(raw + off);
           ai[j] = *reinterpret_cast<const float4*>(raw + SM::A_TILE + off);
         }
-        if (gc >= PS && !mbar_wait(&wfree[ps], ((gc / PS) - 1) & 1)) {
+        if (gc >= PS && !mbar_wait(&wfree[ps], ((gc / PS) - 1) & 1, wait_ns)) {
           ok = false;
           break;
         }
@@ -741,7 +751,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
               lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
             }
           }
-          if (gc >= 1 && !mbar_wait(&afree[k], (gc - 1) & 1)) {
+          if (gc >= 1 && !mbar_wait(&afree[k], (gc - 1) & 1, wait_ns)) {
             ok = false;
             break;
           }
@@ -845,13 +855,13 @@ static int build_operand_V(fbst_plan_s* p, cudaStream_t s) {
   const fbst_info& in = p->info;
   if (in.L % 8 != 0) return FBST_ERR_UNSUPPORTED;  // 16-byte rows for TMA
   const size_t bytes = plane_bytes_G<V>(in);
-  FBST_CUDA_TRY(cudaMalloc(&p->Gtc, bytes));
+  FBST_TRY(plan_alloc(p, bytes, &p->Gtc));
   p->Gtc_bytes = bytes;
   k_tc_split_G<V><<<4096, 256, 0, s>>>(p->G, p->Gtc, in.B, in.N, in.L);
   FBST_CUDA_TRY(cudaGetLastError());
   const int NBW = round16(p->band.max_blocks);
   p->ws_tc_bytes = (size_t)in.B * tc_traits<V>::NPL * NBW * in.L * tc_traits<V>::ESZ;
-  FBST_CUDA_TRY(cudaMalloc(&p->ws_tc, p->ws_tc_bytes));
+  FBST_TRY(plan_alloc(p, p->ws_tc_bytes, &p->ws_tc));
   FBST_CUDA_TRY(cudaMemsetAsync(p->ws_tc, 0, p->ws_tc_bytes, s));
   return FBST_OK;
 }
@@ -860,7 +870,7 @@ static int build_operand_fused(fbst_plan_s* p, cudaStream_t s) {
   const fbst_info& in = p->info;
   if (in.L % 8 != 0) return FBST_ERR_UNSUPPORTED;
   const size_t bytes = (size_t)in.B * 2 * in.N * in.L * sizeof(float);
-  FBST_CUDA_TRY(cudaMalloc(&p->Gtc, bytes));
+  FBST_TRY(plan_alloc(p, bytes, &p->Gtc));
   p->Gtc_bytes = bytes;
   k_tc_planes_f32<<<4096, 256, 0, s>>>(p->G, static_cast<float*>(p->Gtc), in.B, in.N, in.L);
   FBST_CUDA_TRY(cudaGetLastError());
@@ -890,7 +900,8 @@ static int gemm_NB(const fbst_plan_s* p, float2* bhat, int nblk, cudaStream_t s)
   const int smem = tc_smem<V, NB>::BYTES;
   FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc<V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const dim3 grid((in.N + kTileM - 1) / kTileM, in.B, (nblk + NB - 1) / NB);
-  k_dense_tc<V, NB><<<grid, 128, smem, s>>>(mapA, mapB, bhat, in.B, in.N, in.L, nblk, p->d_status);
+  k_dense_tc<V, NB><<<grid, 128, smem, s>>>(mapA, mapB, bhat, in.B, in.N, in.L, nblk, p->d_status,
+                                            p->wait_ns ? p->wait_ns : kWaitNs);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
@@ -936,7 +947,8 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
   k_dense_tc_fused<NB, kPersist><<<grid, kPersist ? 384 : 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk,
                                                                            b0, nbeam, shared_rhs ? 0 : 1,
-                                                                           p->d_status);
+                                                                           p->d_status,
+      p->wait_ns ? p->wait_ns : kWaitNs);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }

@@ -213,19 +213,6 @@ int stream_grid(long long items, int threads) {
   return (int)std::max<long long>(1, std::min<long long>((items + threads - 1) / threads, (long long)sm_count() * 8));
 }
 
-template <typename T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    set_last_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
-    cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? FBST_ERR_OOM : FBST_ERR_CUDA;
-  }
-  return FBST_OK;
-}
-
 bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
 }  // namespace
@@ -246,10 +233,10 @@ struct fbst_null_s {
   null_consts c;
 };
 
+// The object's blocks go back through the plan's allocator (they are in the plan's registry).
 static void free_null(fbst_null_s* n) {
   void* ptrs[] = {n->T, n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) plan_free(n->plan, q);
 }
 
 // One chunk (nb <= max_blocks) of the bracket of Eq. (14): w [nb][B][L] -> wt (may be w).
@@ -258,6 +245,7 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   const int L = in.L, B = in.B;
   const bool tc = n->contraction == FBST_NULL_TF32X3;
   FBST_TRY(launch_beta(in.P_gs, n->XV64, w, n->rhs, n->c, B, tc ? 1 : B, nb, n->plan->tw64, s));
+  n->shadow.wait_ns = n->plan->wait_ns;   // the plan's wait limit applies to the contraction too
   const int r = tc ? launch_dense_tc_shared_rhs(&n->shadow, n->rhs, n->corr, nb, s)
                    : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
   if (r != FBST_OK) return r;
@@ -328,16 +316,20 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
   sh.band = p->band;
   sh.device = p->device;
   sh.d_status = p->d_status;
+  share_allocator(&sh, p);
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int maxb = p->band.max_blocks;
   int r = FBST_OK;
   do {
-    if ((r = dalloc(&n->T, 2 * (size_t)L - 1)) != FBST_OK) break;
-    if ((r = dalloc(&n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
-    if ((r = dalloc(&n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
-    if ((r = dalloc(&n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK) break;
-    if ((r = dalloc(&n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &n->T, 2 * (size_t)L - 1)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK)
+      break;
+    if ((r = plan_alloc_n(p, &n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
+    // Allocated in stream order on the plan's stream: make the blocks usable on `s`.
+    if (cudaStreamSynchronize(p->mem_stream) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     k_null_time<<<(2 * L + 254) / 256, 256, 0, s>>>(n->T, c);
     k_null_Q<<<dim3(std::min((P * L + 255) / 256, 8), L, B), 256, 0, s>>>(n->Q, n->T, c);
     k_null_gs_rows<<<dim3(std::min((in.P_gs + 255) / 256, 16), P), 256, 0, s>>>(p->x64, n->XV64, c, in.P_gs,
@@ -356,10 +348,10 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
       r = st;
       break;
     }
-    cudaFree(n->T);
+    plan_free(p, n->T);
     n->T = nullptr;
     if (contraction == FBST_NULL_TF32X3) {
-      cudaFree(n->Q);
+      plan_free(p, n->Q);
       n->Q = nullptr;
       sh.G = nullptr;
     }
@@ -416,7 +408,6 @@ int fbst_null_launch_count(fbst_null_t n, int nblk) {
 
 int fbst_null_destroy(fbst_null_t n) {
   if (!n) return FBST_OK;
-  cudaDeviceSynchronize();
   free_null(n);
   delete n;
   return FBST_OK;

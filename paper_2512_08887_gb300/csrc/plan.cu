@@ -155,7 +155,7 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
 
   // Memory accounting.
   const size_t c64 = sizeof(float2);
-  size_t tb = 2 * kTwiddleSize * (sizeof(float2) + sizeof(double2));
+  size_t tb = kTwiddleSize * (sizeof(float2) + sizeof(double2));
   tb += c64 * ((size_t)N + (size_t)out->S_time * out->P_time + L);
   tb += c64 * (size_t)L * (g->mx + out->P_space_x + g->bx);
   if (g->kind == FBST_URA && !(g->mx == g->my && g->bx == g->by))
@@ -165,11 +165,15 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
     tb += c64 * (size_t)B * (out->stage2 == FBST_STAGE2_GS_IR1 ? 3 : 2) * out->P_gs;
     tb += c64 * ((size_t)L + (size_t)out->S_rec * out->P_rec + N);
   } else {
+    // G_b in complex64 (FP32 apply), or its tensor-core planes (8 bytes per entry in every
+    // variant; the complex64 G_b is freed once they are built).
     tb += c64 * (size_t)B * N * L;
-    if (out->stage2 != FBST_STAGE2_DENSE_FP32) tb += 2 * c64 * (size_t)B * N * L;
   }
   out->table_bytes = tb;
   out->workspace_bytes = c64 * (size_t)band->max_blocks * ((size_t)L * M + (size_t)B * L);
+  // The pre-split right-hand sides of the BF16x3 and TF32 tensor-core variants.
+  if (out->stage2 == FBST_STAGE2_DENSE_BF16X3 || out->stage2 == FBST_STAGE2_DENSE_TF32)
+    out->workspace_bytes += c64 * (size_t)B * (((size_t)band->max_blocks + 15) / 16 * 16) * L;
   return FBST_OK;
 }
 
@@ -602,8 +606,14 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
   scratch_elems = std::max(scratch_elems, (size_t)B * 2 * in.P_gs);
   double2* scratch = nullptr;
   double2* gen = nullptr;
-  FBST_CUDA_TRY(cudaMallocAsync(&scratch, scratch_elems * sizeof(double2), s));
-  FBST_CUDA_TRY(cudaMallocAsync(&gen, (size_t)B * L * sizeof(double2), s));
+  FBST_TRY(plan_alloc_n(p, &scratch, scratch_elems));
+  {
+    const int r = plan_alloc_n(p, &gen, (size_t)B * L);
+    if (r != FBST_OK) {
+      plan_free(p, scratch);
+      return r;
+    }
+  }
   int rc_status = FBST_OK;
 
   do {
@@ -643,34 +653,36 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
       k_to_c64<<<grid_for((size_t)B * 2 * Pg, 256), 256, 0, s>>>(scratch, p->XV, (size_t)B * 2 * Pg, 1.0);
       if (in.stage2 == FBST_STAGE2_GS_IR1) {
         double2* arows = nullptr;
-        FBST_CUDA_TRY(cudaMallocAsync(&arows, (size_t)B * Pg * sizeof(double2), s));
+        if ((rc_status = plan_alloc_n(p, &arows, (size_t)B * Pg)) != FBST_OK) break;
         k_toeplitz_rows<<<dim3(grid_for(Pg, 256) > 64 ? 64 : grid_for(Pg, 256), B), 256, 0, s>>>(gen, arows, L, Pg);
         rc_status = fft64_rows(arows, B, Pg, p->tw64, -1, s);
         if (rc_status == FBST_OK)
           k_to_c64<<<grid_for((size_t)B * Pg, 256), 256, 0, s>>>(arows, p->Aspec, (size_t)B * Pg, 1.0 / Pg);
-        FBST_CUDA_TRY(cudaFreeAsync(arows, s));
+        plan_free(p, arows);
         if (rc_status != FBST_OK) break;
       }
       k_rec_tables<<<grid_for(L + N, 256), 256, 0, s>>>(p->pre_r, p->post_r, rc, in.S_rec);
       double2* qrows = nullptr;
-      FBST_CUDA_TRY(cudaMallocAsync(&qrows, (size_t)in.S_rec * in.P_rec * sizeof(double2), s));
+      if ((rc_status = plan_alloc_n(p, &qrows, (size_t)in.S_rec * in.P_rec)) != FBST_OK) break;
       k_rec_kernel_rows<<<grid_for((size_t)in.S_rec * in.P_rec, 256), 256, 0, s>>>(qrows, rc, in.S_rec, in.P_rec);
       rc_status = fft64_rows(qrows, in.S_rec, in.P_rec, p->tw64, -1, s);
       if (rc_status == FBST_OK)
         k_to_c64<<<grid_for((size_t)in.S_rec * in.P_rec, 256), 256, 0, s>>>(qrows, p->qspec_r, (size_t)in.S_rec * in.P_rec, 1.0 / in.P_rec);
-      FBST_CUDA_TRY(cudaFreeAsync(qrows, s));
+      plan_free(p, qrows);
       if (rc_status != FBST_OK) break;
     } else {
       if ((rc_status = dense_G(scratch, p->G, rc, B, Pg, p->tw64, s)) != FBST_OK) break;
       if (in.stage2 != FBST_STAGE2_DENSE_FP32) {
         if ((rc_status = build_dense_tc_operand(p, s)) != FBST_OK) break;
+        plan_free(p, p->G);        // the tensor-core planes replace it (the free is stream-ordered)
+        p->G = nullptr;
       }
     }
     FBST_CUDA_TRY(cudaGetLastError());
   } while (0);
 
-  FBST_CUDA_TRY(cudaFreeAsync(scratch, s));
-  FBST_CUDA_TRY(cudaFreeAsync(gen, s));
+  plan_free(p, scratch);
+  plan_free(p, gen);
   FBST_CUDA_TRY(cudaStreamSynchronize(s));
   if (rc_status != FBST_OK) return rc_status;
   int st = 0;

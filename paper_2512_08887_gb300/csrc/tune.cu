@@ -68,7 +68,11 @@ int fbst_autotune(fbst_plan_t p, int nblk, void* stream, int* shapes4) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const fbst_info& in = p->info;
   float2* y = nullptr;
-  FBST_CUDA_TRY(cudaMalloc(&y, sizeof(float2) * (size_t)nblk * in.M * in.N));
+  {
+    const int ra = plan_alloc_n(p, &y, (size_t)nblk * in.M * in.N);
+    if (ra != FBST_OK) return ra;
+  }
+  FBST_CUDA_TRY(cudaStreamSynchronize(p->mem_stream));   // allocated in order on the plan's stream
   FBST_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(float2) * (size_t)nblk * in.M * in.N, s));
   int r = FBST_OK;
   // Temporal chirp-z.
@@ -110,7 +114,7 @@ int fbst_autotune(fbst_plan_t p, int nblk, void* stream, int* shapes4) {
     p->shape_space = pick;
   }
   cudaStreamSynchronize(s);
-  cudaFree(y);
+  plan_free(p, y);
   if (r == FBST_OK && shapes4) r = fbst_get_shapes(p, shapes4);
   return r;
 }

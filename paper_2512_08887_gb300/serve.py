@@ -8,12 +8,16 @@ A request is one block of N snapshots of one of the server's arrays (a plan). Th
   order: requests whose array is already in an in-flight batch wait (a plan's workspace serves one
   batch at a time), at most `max_per_array` requests of one array go into a batch (the plan's
   block capacity), and admission stops at the first request whose device buffers (input + output)
-  would exceed the memory budget, so large requests are not starved;
-* the executor copies the batch's inputs to the device, runs all its arrays in one grouped launch
-  sequence (fbst_batch_enqueue; a batch of one request runs fbst_execute on the array's resident
-  one-block buffers), copies the outputs back and records an event, all on one stream;
-  batches on different streams overlap on the GPU;
-* completions free the requests' memory and their arrays, and admit waiting work.
+  would exceed the memory budget or the batch's memory (one stream's arena), so large requests
+  are not starved;
+* the executor copies the batch's inputs into its stream's resident device arena, runs all its
+  arrays in one grouped launch sequence (fbst_batch_enqueue; a batch of one request runs
+  fbst_execute), copies the outputs into the stream's resident pinned host arena and records an
+  event, all on one stream; batches on different streams overlap on the GPU. The arenas are sized
+  from the device's free memory when the executor starts, and nothing is allocated in the loop;
+* completions free the requests' memory and their arrays, and admit waiting work;
+* a batch whose submission fails (a malformed request, an error of the library) is reported: its
+  requests complete with `error` set and the loop goes on serving the others.
 
 The scheduling policy (`Scheduler`) is plain Python and is tested on the CPU with a simulated
 executor; `GPUExecutor` is the device side. `serve_plain` is the comparison: one request at a
@@ -37,15 +41,19 @@ class Request:
     t_done: float | None = None
     out: object = None        # host output block [1][B][N], filled on completion if kept
     batch_id: int = -1
+    error: str | None = None  # set when the request's batch could not be run
 
 
 class Scheduler:
     """Admission by device memory and formation of batches (no GPU work)."""
 
-    def __init__(self, req_bytes, mem_budget: int, max_per_array: int, req_work=None, max_batch_work=None):
+    def __init__(self, req_bytes, mem_budget: int, max_per_array: int, req_work=None, max_batch_work=None,
+                 max_batch_bytes=None):
         self.req_bytes = list(req_bytes)     # device bytes one request of array i holds while active
         self.mem_budget = int(mem_budget)
         self.max_per_array = int(max_per_array)
+        # Optional cap on one batch's device bytes (the executor's per-stream arena).
+        self.max_batch_bytes = max_batch_bytes
         # Optional cap on the work of one batch (e.g. beam-samples): later requests wait for the
         # next stream slot, so a backlog becomes several pipelined batches instead of one long one.
         self.req_work = list(req_work) if req_work is not None else None
@@ -60,7 +68,7 @@ class Scheduler:
         self.pending.append(req)
 
     def form_batch(self, now: float) -> list:
-        batch, per_array, waiting, work = [], {}, collections.deque(), 0
+        batch, per_array, waiting, work, nbytes = [], {}, collections.deque(), 0, 0
         while self.pending:
             r = self.pending.popleft()
             a = r.array
@@ -73,6 +81,10 @@ class Scheduler:
             if batch and self.max_batch_work is not None and work + self.req_work[a] > self.max_batch_work:
                 waiting.append(r)
                 break
+            if batch and self.max_batch_bytes is not None and nbytes + self.req_bytes[a] > self.max_batch_bytes:
+                waiting.append(r)
+                break
+            nbytes += self.req_bytes[a]
             if self.req_work is not None:
                 work += self.req_work[a]
             per_array[a] = per_array.get(a, 0) + 1
@@ -112,21 +124,33 @@ def run_loop(requests: list, scheduler: Scheduler, executor, clock=time.perf_cou
         if executor.can_submit() and scheduler.pending:
             batch = scheduler.form_batch(now)
             if batch:
-                executor.submit(batch, now)
+                try:
+                    executor.submit(batch, now)
+                except Exception as e:                  # report the batch, keep serving the rest
+                    t = clock() - t0
+                    for r in batch:
+                        r.error = f"{type(e).__name__}: {e}"
+                        r.t_done = t
+                    scheduler.complete(batch)
+                    done += len(batch)
     return summarize(requests, executor_units=getattr(executor, "units", None), batches=scheduler.batches,
                      peak_mem=scheduler.peak_mem)
 
 
 def summarize(requests: list, executor_units=None, batches=None, peak_mem=None) -> dict:
+    """Latency percentiles and throughput over the requests that were served (failed ones are
+    counted apart)."""
     import numpy as np
-    lat = np.array([r.t_done - r.t_arrival for r in requests])
+    ok = [r for r in requests if r.error is None]
+    lat = np.array([r.t_done - r.t_arrival for r in ok]) if ok else np.zeros(1)
     span = max(r.t_done for r in requests) - min(r.t_arrival for r in requests)
-    out = {"requests": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+    out = {"requests": len(requests), "failed": len(requests) - len(ok),
+           "p50_ms": float(np.percentile(lat, 50) * 1e3),
            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
            "span_s": float(span)}
     if executor_units is not None:
-        units = sum(executor_units[r.array] for r in requests)
-        out["beam_samples_per_s"] = float(units / span)
+        units = sum(executor_units[r.array] for r in ok)
+        out["beam_samples_per_s"] = float(units / span) if span > 0 else 0.0
     if batches is not None:
         out["batches"] = batches
         out["mean_batch"] = len(requests) / max(1, batches)
@@ -136,9 +160,17 @@ def summarize(requests: list, executor_units=None, batches=None, peak_mem=None) 
 
 
 class GPUExecutor:
-    """Device side: one grouped launch sequence per batch on one of `n_streams` CUDA streams."""
+    """Device side: one grouped launch sequence per batch on one of `n_streams` CUDA streams.
 
-    def __init__(self, plans, n_streams: int = 3, keep_outputs: bool = False):
+    Each stream owns a resident device arena and a resident pinned host arena of `arena_bytes`
+    (default: a share of the device's free memory, at most 256 MiB); a batch's inputs, outputs and
+    host copies of the outputs are carved from its stream's arenas, so the loop allocates nothing.
+    `device_budget` is the memory the scheduler should admit against (all arenas)."""
+
+    ALIGN = 256
+
+    def __init__(self, plans, n_streams: int = 3, keep_outputs: bool = False, arena_bytes: int | None = None,
+                 free_fraction: float = 0.25):
         import torch
         from ._native import Batch
         self.torch = torch
@@ -150,82 +182,89 @@ class GPUExecutor:
         self.keep = keep_outputs
         self.dims = [(p.M, p.N, p.B) for p in self.plans]
         self.units = [p.B * p.N for p in self.plans]
-        self.out_pool = collections.defaultdict(list)   # pinned host output buffers per array
-        # One-block device buffers per array for single-request batches. The scheduler never has
-        # two batches of the same array in flight, so they are never used twice at once.
-        self.single = {}
+        if arena_bytes is None:
+            free_bytes, _ = torch.cuda.mem_get_info()
+            arena_bytes = min(256 << 20, int(free_bytes * free_fraction) // n_streams)
+        self.arena_bytes = int(arena_bytes) // self.ALIGN * self.ALIGN
+        self.dev_arena = [torch.empty(self.arena_bytes, dtype=torch.uint8, device="cuda") for _ in range(n_streams)]
+        self.host_arena = [torch.empty(self.arena_bytes, dtype=torch.uint8).pin_memory() for _ in range(n_streams)]
+        self.device_budget = self.arena_bytes * n_streams
+
+    def request_bytes(self, a: int) -> int:
+        """Device bytes of one request of array a in an arena (input and output block, aligned)."""
+        M, N, B = self.dims[a]
+        return self._aligned(8 * M * N) + self._aligned(8 * B * N)
+
+    def _aligned(self, n: int) -> int:
+        return (n + self.ALIGN - 1) // self.ALIGN * self.ALIGN
 
     def can_submit(self) -> bool:
         return bool(self.free)
 
-    def _out_buffer(self, a: int):
-        if self.out_pool[a]:
-            return self.out_pool[a].pop()
-        M, N, B = self.dims[a]
-        return self.torch.empty((1, B, N), dtype=self.torch.complex64).pin_memory()
-
-    def _submit_single(self, r, st):
-        """One request: fbst_execute on the array's resident one-block buffers (no grouping)."""
-        torch = self.torch
-        a = r.array
-        if a not in self.single:
-            M, N, B = self.dims[a]
-            self.single[a] = (torch.empty((1, M, N), dtype=torch.complex64, device="cuda"),
-                              torch.empty((1, B, N), dtype=torch.complex64, device="cuda"))
-        yd, od = self.single[a]
-        yd.copy_(r.y, non_blocking=True)
-        self.plans[a].execute(yd, od, 1, st)
-        h = self._out_buffer(a)
-        h.copy_(od, non_blocking=True)
-        return [], [(r, h)]
+    def _carve(self, arena, off: int, shape):
+        n = 8 * shape[0] * shape[1] * shape[2]
+        if off + n > self.arena_bytes:
+            raise MemoryError(f"batch needs more than the {self.arena_bytes >> 20} MiB arena of a stream")
+        return arena[off:off + n].view(self.torch.complex64).view(shape), off + self._aligned(n)
 
     def submit(self, batch: list, now: float) -> None:
         torch = self.torch
         si = self.free.pop(0)
+        try:
+            self._submit(si, batch)
+        except Exception:
+            self.free.insert(0, si)
+            raise
+        for r in batch:
+            r.t_launch = now
+
+    def _submit(self, si: int, batch: list) -> None:
+        torch = self.torch
         st = self.streams[si]
-        if len(batch) == 1:
-            with torch.cuda.stream(st):
-                keep, hosts = self._submit_single(batch[0], st)
-                ev = torch.cuda.Event()
-                ev.record(st)
-            batch[0].t_launch = now
-            self.inflight.append((si, ev, batch, keep, hosts))
-            return
+        dev, host = self.dev_arena[si], self.host_arena[si]
         groups = collections.defaultdict(list)
         for r in batch:
             groups[r.array].append(r)
         n = len(self.plans)
-        ys, outs, nb, keep, hosts = [0] * n, [0] * n, [0] * n, [], []
+        ys, outs, nb, hosts = [0] * n, [0] * n, [0] * n, []
+        off = hoff = 0
+        views = {}
+        for a, rs in groups.items():
+            M, N, B = self.dims[a]
+            yd, off = self._carve(dev, off, (len(rs), M, N))
+            od, off = self._carve(dev, off, (len(rs), B, N))
+            oh, hoff = self._carve(host, hoff, (len(rs), B, N))
+            for r in rs:
+                if tuple(r.y.shape[-2:]) != (M, N):
+                    raise ValueError(f"request {r.rid}: input {tuple(r.y.shape)} does not fit array {a} ({M}x{N})")
+            views[a] = (yd, od, oh)
         with torch.cuda.stream(st):
             for a, rs in groups.items():
-                M, N, B = self.dims[a]
-                yd = torch.empty((len(rs), M, N), dtype=torch.complex64, device="cuda")
-                od = torch.empty((len(rs), B, N), dtype=torch.complex64, device="cuda")
+                yd, od, oh = views[a]
                 for j, r in enumerate(rs):
-                    yd[j].copy_(r.y[0], non_blocking=True)
+                    yd[j].copy_(r.y.reshape(yd.shape[1:]), non_blocking=True)
                 ys[a], outs[a], nb[a] = yd, od, len(rs)
-                keep += [yd, od]
-            self.batch.enqueue(ys, outs, nb, st)
+            if len(batch) == 1:
+                a = batch[0].array
+                self.plans[a].execute(ys[a], outs[a], 1, st)
+            else:
+                self.batch.enqueue(ys, outs, nb, st)
             for a, rs in groups.items():
-                for j, r in enumerate(rs):
-                    h = self._out_buffer(a)
-                    h.copy_(outs[a][j:j + 1], non_blocking=True)
-                    hosts.append((r, h))
+                yd, od, oh = views[a]
+                oh.copy_(od, non_blocking=True)
+                hosts += [(r, oh[j:j + 1]) for j, r in enumerate(rs)]
             ev = torch.cuda.Event()
             ev.record(st)
-        for r in batch:
-            r.t_launch = now
-        self.inflight.append((si, ev, batch, keep, hosts))
+        self.inflight.append((si, ev, batch, hosts))
 
     def poll(self) -> list:
         done, still = [], []
         for item in self.inflight:
-            si, ev, batch, keep, hosts = item
+            si, ev, batch, hosts = item
             if ev.query():
-                for r, h in hosts:
-                    if self.keep:
+                if self.keep:
+                    for r, h in hosts:
                         r.out = h.clone()
-                    self.out_pool[r.array].append(h)
                 self.free.append(si)
                 done.append(batch)
             else:

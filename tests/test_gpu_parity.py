@@ -293,3 +293,26 @@ def test_execute_c2_full_size_tf32x3_sampled_beams():
     assert O.rel_l2(got[:, beams], ref) < TOL_E2E
     assert per_beam_err(got[:, beams], ref) < TOL_E2E
     assert np.isfinite(got).all()
+
+
+@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_bf16x3"])
+def test_tensor_core_wait_that_runs_out_reports_timeout_and_recovers(rng, stage2):
+    # Failure detection without a fault: a wait limit of 1 ns makes the pipeline waits of the
+    # tensor-core kernel run out (nothing can complete that fast). The kernel must record
+    # FBST_ERR_TIMEOUT, drain its own copies and MMAs, free tensor memory and return; the status is
+    # read and cleared by fbst_sync_status, and the next call with the default limit is correct.
+    plan, pb = make("ula", 64, 1, 64, 1, 512, 0.5, stage2=stage2, max_blocks=16)
+    y = crandn(rng, 16, 64, 512)
+    w = O.fan_coefficients(pb, y[:2]).astype(np.complex64)
+    wd = dev(np.concatenate([w, np.zeros((14,) + w.shape[1:], np.complex64)]))
+    out = nan_like((16, 64, 512))
+    plan.set_wait_limit(1)
+    plan.toeplitz_apply(wd, out, 16)
+    assert plan.sync_status() == -5                    # FBST_ERR_TIMEOUT
+    assert plan.sync_status() == 0                     # read and cleared
+    plan.set_wait_limit(0)
+    out2 = nan_like((16, 64, 512))
+    plan.toeplitz_apply(wd, out2, 16)
+    assert plan.sync_status() == 0
+    got = out2.cpu().numpy()[:2]
+    assert O.rel_l2(got, O.Stage2Factors(pb).apply(w)) < TC_TOL[stage2]

@@ -29,8 +29,9 @@ def test_results_are_the_same_alone_and_in_the_mix():
             blocks.append(torch.from_numpy(y.astype(np.complex64)).pin_memory())
         pools.append(blocks)
     reqs = serve.poisson_requests(2e4, 60, pools, seed=5)
-    sched = serve.Scheduler([8 * (p.M * p.N + p.B * p.N) for p in plans], 1 << 30, max_per_array=4)
     ex = serve.GPUExecutor(plans, n_streams=3, keep_outputs=True)
+    sched = serve.Scheduler([ex.request_bytes(a) for a in range(len(plans))], ex.device_budget, max_per_array=4,
+                            max_batch_bytes=ex.arena_bytes)
     stats = serve.run_loop(reqs, sched, ex)
     ex.close()
     assert stats["requests"] == 60 and stats["mean_batch"] > 1

@@ -104,3 +104,47 @@ def test_poisson_arrivals_have_the_requested_rate():
     reqs = poisson_requests(1e3, 5000, [[None]] * 4, seed=1)
     t = np.array([r.t_arrival for r in reqs])
     assert abs(len(t) / t[-1] / 1e3 - 1) < 0.05
+
+
+class FailingExecutor(SimExecutor):
+    """A SimExecutor whose k-th submission raises (a host-side injected failure: the library or a
+    malformed request refusing the batch) before anything runs."""
+
+    def __init__(self, *a, fail_on=(3,), **kw):
+        super().__init__(*a, **kw)
+        self.calls, self.fail_on = 0, set(fail_on)
+
+    def submit(self, batch, now):
+        self.calls += 1
+        if self.calls in self.fail_on:
+            raise RuntimeError("injected: fbst_batch_enqueue failed")
+        super().submit(batch, now)
+
+
+def test_failed_batches_are_reported_and_the_rest_is_served():
+    reqs = poisson_requests(5e4, 300, [[None]] * 5, seed=8)
+    sched = Scheduler([1 << 20] * 5, 1 << 30, max_per_array=4)
+    clock = FakeClock()
+    ex = FailingExecutor(clock, 3, 5e-5, [100] * 5, fail_on=(2, 5, 9))
+    stats = run_loop(reqs, sched, ex, clock=clock)
+    failed = [r for r in reqs if r.error is not None]
+    assert failed and all("injected" in r.error for r in failed)
+    assert stats["failed"] == len(failed) and stats["requests"] == len(reqs)
+    # Every other request was served after the failures, and the bookkeeping is clean.
+    assert all(r.t_done is not None and r.t_done >= r.t_admit for r in reqs if r.error is None)
+    assert max(r.batch_id for r in failed) < max(r.batch_id for r in reqs if r.error is None)
+    assert sched.mem_used == 0 and not sched.busy and not sched.pending
+    assert stats["beam_samples_per_s"] > 0
+
+
+def test_batch_bytes_stay_within_one_stream_arena():
+    reqs = poisson_requests(1e6, 200, [[None]] * 6, seed=4)
+    req_bytes = [1 << (20 + a % 3) for a in range(6)]
+    cap = 5 << 20
+    sched = Scheduler(req_bytes, 1 << 30, max_per_array=8, max_batch_bytes=cap)
+    clock = FakeClock()
+    run_loop(reqs, sched, SimExecutor(clock, 3, 5e-5, [100] * 6), clock=clock)
+    per_batch = {}
+    for r in reqs:
+        per_batch[r.batch_id] = per_batch.get(r.batch_id, 0) + req_bytes[r.array]
+    assert max(per_batch.values()) <= cap and len(per_batch) > 1
