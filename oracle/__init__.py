@@ -7,7 +7,8 @@ Parity status of each function is stated in fbst_oracle's docstrings; every func
 the tests in tests/test_oracle_pins.py except the size of the noise-free bias of a plane wave,
 which the paper gives no number for ("parity unpinned": only a sanity bound is checked). The
 beamspace interference nulling of Eq. (14) is pinned by tests/test_oracle_nulling.py, and the
-non-uniform arrays of Sec. IX (make_problem(..., offsets=...)) by tests/test_oracle_nonuniform.py.
+non-uniform arrays of Sec. IX (make_problem(..., offsets=...)) by tests/test_oracle_nonuniform.py, and
+the off-grid beams of Sec. VIII-A by tests/test_oracle_offgrid.py.
 """
 from .fbst_oracle import (  # noqa: F401
     Problem,
@@ -19,6 +20,12 @@ from .fbst_oracle import (  # noqa: F401
     stage1_space,
     fan_coefficients,
     gram,
+    gram_direction,
+    natural_spline_weights,
+    interp_window,
+    offgrid_terms,
+    OffGridFactors,
+    fbst_offgrid,
     fbst,
     dense_operator,
     cross_gram,

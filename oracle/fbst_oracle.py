@@ -87,9 +87,13 @@ class Problem:
         """ell' = ell - L/2 for the paper's ell = 1..L (Eq. (3))."""
         return np.arange(1, self.L + 1, dtype=np.float64) - self.L / 2
 
-    def tau(self, beams=None) -> np.ndarray:
-        """tau_{b,m}/T_s = rho*(u_b*px_m + v_b*py_m), shape (len(beams), M)."""
-        d = self.directions if beams is None else self.directions[np.asarray(beams)]
+    def tau(self, beams=None, directions=None) -> np.ndarray:
+        """tau_{b,m}/T_s = rho*(u_b*px_m + v_b*py_m), shape (len(beams), M); or, given
+        `directions` ((n, 2) direction cosines, on or off the grid), the same for those."""
+        if directions is not None:
+            d = np.atleast_2d(np.asarray(directions, dtype=np.float64))
+        else:
+            d = self.directions if beams is None else self.directions[np.asarray(beams)]
         return self.rho * (d @ self.positions.T)
 
 
@@ -111,12 +115,13 @@ def make_problem(kind: str, mx: int, my: int, bx: int, by: int, N: int, frac_bw:
 # Explicit matrices (Eq. (6) and Eq. (7)) -- used directly on small problems and as pins.
 # ----------------------------------------------------------------------------------------------
 
-def F_theta(pb: Problem, b: int) -> np.ndarray:
-    """The MN x L matrix of Eq. (6) for beam b; row m*N + n is (sensor m, snapshot n).
+def F_theta(pb: Problem, b: int, direction=None) -> np.ndarray:
+    """The MN x L matrix of Eq. (6) for beam b (or for the direction cosines `direction`, on or
+    off the grid); row m*N + n is (sensor m, snapshot n).
 
     [F]_{(m,n), ell} = exp(-2j*pi*f_c*tau_m) * exp(j*omega_ell*(t_n - tau_m)).
     """
-    tau = pb.tau([b])[0]                      # (M,)
+    tau = pb.tau([b])[0] if direction is None else pb.tau(directions=direction)[0]   # (M,)
     n = np.arange(pb.N, dtype=np.float64)
     t_minus_tau = n[None, :] - tau[:, None]   # (M, N)
     carrier = np.exp(-TWO_PI_J * tau / pb.frac_bw)[:, None, None]
@@ -144,14 +149,14 @@ def stage1_time(pb: Problem, y: np.ndarray) -> np.ndarray:
     return np.asarray(y, dtype=np.complex128) @ E
 
 
-def stage1_space(pb: Problem, yhat: np.ndarray, beams=None, chunk: int = 64) -> np.ndarray:
+def stage1_space(pb: Problem, yhat: np.ndarray, beams=None, chunk: int = 64, directions=None) -> np.ndarray:
     """w[..., b, ell] = sum_m yhat[..., m, ell] exp(2j*pi*(1/fb + eps*ell'/L)*tau_{b,m}).
 
     This is the second sum of Sec. IV (and the two array sums of App. B written as one sum over
     the elements). yhat has shape (..., M, L); the result has shape (..., nbeams, L).
     """
     yhat = np.asarray(yhat, dtype=np.complex128)
-    tau = pb.tau(beams)                                   # (nb, M)
+    tau = pb.tau(beams, directions)                       # (nb, M)
     lead = yhat.shape[:-2]
     Y = yhat.reshape((-1,) + yhat.shape[-2:])             # (K, M, L)
     out = np.empty((Y.shape[0], tau.shape[0], pb.L), dtype=np.complex128)
@@ -164,9 +169,10 @@ def stage1_space(pb: Problem, yhat: np.ndarray, beams=None, chunk: int = 64) -> 
     return out.reshape(lead + (tau.shape[0], pb.L))
 
 
-def fan_coefficients(pb: Problem, y: np.ndarray, beams=None) -> np.ndarray:
-    """w = F_b^H y for every beam: (..., M, N) -> (..., nbeams, L)."""
-    return stage1_space(pb, stage1_time(pb, y), beams)
+def fan_coefficients(pb: Problem, y: np.ndarray, beams=None, directions=None) -> np.ndarray:
+    """w = F_b^H y for every beam: (..., M, N) -> (..., nbeams, L); with `directions`, the exact
+    coefficient vectors of those (possibly off-grid) directions instead."""
+    return stage1_space(pb, stage1_time(pb, y), beams, directions=directions)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -174,7 +180,13 @@ def fan_coefficients(pb: Problem, y: np.ndarray, beams=None) -> np.ndarray:
 # ----------------------------------------------------------------------------------------------
 
 def gram(pb: Problem, b: int) -> np.ndarray:
-    """A_b = F_b^H F_b + delta I by direct sums (Eq. (5); its entries are those of Sec. V).
+    """A_b = F_b^H F_b + delta I of grid beam b (see gram_direction)."""
+    return gram_direction(pb, pb.directions[b])
+
+
+def gram_direction(pb: Problem, direction) -> np.ndarray:
+    """A = F^H F + delta I by direct sums for the direction cosines `direction` = (u, v), on or off
+    the grid (Eq. (5); its entries are those of Sec. V).
 
     With E[n, ell] = exp(j*omega_ell*t_n) and phi[ell, m] = exp(-j*omega_ell*tau_m), the entry
     [F_b]_{(m,n),ell} is carrier_m * E[n,ell] * phi[ell,m], so
@@ -182,7 +194,7 @@ def gram(pb: Problem, b: int) -> np.ndarray:
     the elementwise product of two Gram matrices (the unit-modulus carrier drops out).
     """
     E = F_u(pb)                                                                  # (N, L)
-    tau = pb.tau([b])[0]
+    tau = pb.tau(directions=direction)[0]
     phi = np.exp(-TWO_PI_J * pb.epsilon * np.multiply.outer(pb.lprime, tau) / pb.L)  # (L, M)
     A = (E.conj().T @ E) * (phi.conj() @ phi.T)
     A[np.diag_indices(pb.L)] += pb.delta
@@ -291,6 +303,118 @@ def fbst_nulled(pb: Problem, y: np.ndarray, interferers, beams=None,
     w = fan_coefficients(pb, y, factors.out.beams)
     w_int = fan_coefficients(pb, y, factors.interferers) if factors.interferers else None
     return factors.out.apply(factors.coefficients(w, w_int))
+
+
+# ----------------------------------------------------------------------------------------------
+# Off-grid beams by interpolation of beam vectors (Sec. VIII-A)
+# ----------------------------------------------------------------------------------------------
+
+def natural_spline_weights(x: np.ndarray, xq: float) -> np.ndarray:
+    """Weights c with s(xq) = sum_i c_i f_i, where s is the natural cubic spline through the points
+    (x_i, f_i) (x increasing): cubic on every interval, continuous with its first and second
+    derivatives at the inner knots, second derivative zero at both ends. The spline is linear in
+    the data, so c_i is the spline of the unit data e_i evaluated at xq.
+
+    With h_i = x_{i+1} - x_i and moments s''(x_i) = Mo_i, the inner conditions read
+    h_{i-1} Mo_{i-1} + 2 (h_{i-1} + h_i) Mo_i + h_i Mo_{i+1} = 6 ((f_{i+1} - f_i)/h_i - (f_i - f_{i-1})/h_{i-1})
+    with Mo_0 = Mo_{n-1} = 0; on [x_i, x_{i+1}] with a = x_{i+1} - xq, b = xq - x_i,
+    s = (Mo_i a^3 + Mo_{i+1} b^3) / (6 h_i) + (f_i - Mo_i h_i^2 / 6) a / h_i + (f_{i+1} - Mo_{i+1} h_i^2 / 6) b / h_i.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    if n == 1:
+        return np.ones(1)
+    h = np.diff(x)
+    F = np.eye(n)                                  # column j: the unit data e_j
+    Mo = np.zeros((n, n))
+    if n > 2:
+        A = np.zeros((n - 2, n - 2))
+        rhs = np.zeros((n - 2, n))
+        for r, i in enumerate(range(1, n - 1)):
+            if r > 0:
+                A[r, r - 1] = h[i - 1]
+            A[r, r] = 2.0 * (h[i - 1] + h[i])
+            if r < n - 3:
+                A[r, r + 1] = h[i]
+            rhs[r] = 6.0 * ((F[i + 1] - F[i]) / h[i] - (F[i] - F[i - 1]) / h[i - 1])
+        Mo[1:n - 1] = np.linalg.solve(A, rhs)
+    i = int(np.clip(np.searchsorted(x, xq, side="right") - 1, 0, n - 2))
+    a, b = x[i + 1] - xq, xq - x[i]
+    return ((Mo[i] * a ** 3 + Mo[i + 1] * b ** 3) / (6.0 * h[i])
+            + (F[i] - Mo[i] * h[i] ** 2 / 6.0) * a / h[i] + (F[i + 1] - Mo[i + 1] * h[i] ** 2 / 6.0) * b / h[i])
+
+
+def interp_window(n_grid: int, coord: float, K: int = 8) -> int:
+    """First index of the K consecutive grid indices around the continuous grid coordinate `coord`
+    (K/2 on each side of the interval that holds it), moved inward at the ends of the grid."""
+    K = min(K, n_grid)
+    first = int(np.floor(coord)) - (K // 2 - 1)
+    return int(min(max(first, 0), n_grid - K))
+
+
+def offgrid_terms(pb: Problem, direction, K: int = 8) -> list:
+    """(grid beam, weight) pairs that form the interpolated beam vector of `direction` = (u, v):
+    a natural cubic spline along u through the K nearest grid beams (the beam grid is uniform in
+    the direction cosine, u_a = -1 + 2a/bx), and for a rectangular array the same along v (the
+    tensor product of the two one-dimensional splines)."""
+    u, v = float(direction[0]), float(direction[1])
+
+    def axis(nb, c):
+        coord = (c + 1.0) * nb / 2.0                 # grid index of c (u_a = -1 + 2a/nb)
+        first = interp_window(nb, coord, K)
+        k = min(K, nb)
+        idx = np.arange(first, first + k)
+        return idx, natural_spline_weights(-1.0 + 2.0 * idx / nb, c)
+
+    ia, wa = axis(pb.bx, u)
+    if pb.geom.kind == "ula":
+        return [(int(a), float(w)) for a, w in zip(ia, wa)]
+    ic, wc = axis(pb.by, v)
+    return [(int(a) * pb.by + int(c), float(x * z)) for a, x in zip(ia, wa) for c, z in zip(ic, wc)]
+
+
+class OffGridFactors:
+    """Per-plan part of the off-grid beams of Sec. VIII-A: the interpolation terms of every
+    requested direction and the LU factors of its own A = F^H F + delta I (an off-grid direction
+    has its own regularised least-squares problem, Eq. (5))."""
+
+    def __init__(self, pb: Problem, directions, K: int = 8):
+        self.pb = pb
+        self.directions = np.atleast_2d(np.asarray(directions, dtype=np.float64))
+        self.terms = [offgrid_terms(pb, d, K) for d in self.directions]
+        self.beams = sorted({b for t in self.terms for b, _ in t})
+        self.Fu = F_u(pb)
+        self.lu = [scipy.linalg.lu_factor(gram_direction(pb, d)) for d in self.directions]
+
+    def interpolate(self, w_grid: np.ndarray) -> np.ndarray:
+        """w_grid: (nblk, B, L), every grid beam -> interpolated (nblk, ndirs, L)."""
+        w_grid = np.asarray(w_grid, dtype=np.complex128)
+        out = np.zeros(w_grid.shape[:-2] + (len(self.terms), self.pb.L), dtype=np.complex128)
+        for k, t in enumerate(self.terms):
+            for b, c in t:
+                out[..., k, :] += c * w_grid[..., b, :]
+        return out
+
+    def apply(self, wstar: np.ndarray) -> np.ndarray:
+        """Stage 2 of the off-grid directions: (nblk, ndirs, L) -> (nblk, ndirs, N)."""
+        wstar = np.asarray(wstar, dtype=np.complex128)
+        out = np.empty(wstar.shape[:-1] + (self.pb.N,), dtype=np.complex128)
+        for i, lu in enumerate(self.lu):
+            out[:, i, :] = (self.Fu @ scipy.linalg.lu_solve(lu, wstar[:, i, :].T)).T
+        return out
+
+
+def fbst_offgrid(pb: Problem, y: np.ndarray, directions, factors: OffGridFactors | None = None) -> np.ndarray:
+    """Off-grid beams (Sec. VIII-A): y (nblk, M, N) -> (nblk, ndirs, N), the beam vector of each
+    direction interpolated from the grid beams' w_b, then F_u A^{-1} of that direction."""
+    y = np.asarray(y)
+    if y.ndim == 2:
+        y = y[None]
+    if factors is None:
+        factors = OffGridFactors(pb, directions)
+    w = np.zeros(y.shape[:-2] + (pb.B, pb.L), dtype=np.complex128)
+    w[..., factors.beams, :] = fan_coefficients(pb, y, factors.beams)
+    return factors.apply(factors.interpolate(w))
 
 
 # ----------------------------------------------------------------------------------------------
