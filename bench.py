@@ -9,7 +9,7 @@ oracle is measured and reported on every run); --stage2 gs_ir1 selects the Gohbe
 dense_fp32 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload ULA1024|C2|C3|C4|C5|C2N] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|C2|C3|C4|C5|C2N|OG] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
 stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
@@ -545,6 +545,165 @@ def run_null(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_offgrid(args) -> None:
+    """OG: off-grid beams (Sec. VIII-A) on a 2x oversampled grid, the paper's setting: 256-element
+    ULA, 512 grid beams, N = 256, 64 blocks per step, 64 off-grid directions, each interpolated from
+    8 grid beam vectors; one step = fbst_offgrid_execute (stage 1, interpolation, stage 2 of the
+    off-grid directions)."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload OG runs on one GPU (replicas of it scale like the plain transform)")
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300.build import build
+    from synth import configs
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    M, B, N, nblk, ndir = 256, 512, 256, args.nblk or 64, 64
+    d = configs.config_data("C2", nblk=nblk)                  # the 256-element record of C2
+    dirs = np.stack([np.random.default_rng(2026).uniform(-0.98, 0.98, ndir), np.zeros(ndir)], axis=1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    # The grid plan provides stage 1 and the workspace; its own stage 2 is not used here.
+    plan = fb.Plan(fb.make_geometry("ula", M, 1, B, 1), N, fb.make_band(0.5, stage2="gs", max_blocks=nblk))
+    info = plan.info
+    L = info.L
+    t0 = time.perf_counter()
+    og = fb.OffGrid(plan, dirs)
+    t_create = time.perf_counter() - t0
+    y = torch.from_numpy(d["y"]).to(dev)
+    out = torch.empty((nblk, ndir, N), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    og.execute(y, out, nblk)
+    if plan.sync_status() != 0:
+        raise SystemExit("device status word set after the off-grid transform")
+    pb = O.make_problem("ula", M, 1, B, 1, N, frac_bw=info.fb_num / info.fb_den, epsilon=info.eps_num / info.eps_den,
+                        delta=info.delta, L=L)
+    sel = [0, 17, 40, 63]
+    fac = O.OffGridFactors(pb, dirs[sel])
+    ref = fac.apply(fac.interpolate(O.fan_coefficients(pb, d["y"][:2])))
+    rel_err = O.rel_l2(out[:2].cpu().numpy()[:, sel], ref)
+    exact = fac.apply(O.fan_coefficients(pb, d["y"][:2], directions=dirs[sel]))
+    interp_vs_exact = O.rel_l2(ref, exact)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        og.execute(y, out, nblk)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        og.execute(y, out, nblk)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    value = float(nblk) * ndir * N * args.steps / (sum(step_ms) / 1e3)
+
+    # Per-stage live timing: stage 1 (two C-ABI calls), the interpolation, the interpolation + the
+    # off-grid stage 2 (fbst_offgrid_apply), each with events on the launching stream.
+    kin = min(args.steps, 200)
+    yhat = torch.empty((nblk, L, M), dtype=torch.complex64, device=dev)
+    wbuf = torch.empty((nblk, B, L), dtype=torch.complex64, device=dev)
+    wstar = torch.empty((nblk, ndir, L), dtype=torch.complex64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(kin)]
+    for i in range(kin):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.czt_time(y, yhat, nblk)
+        ev[i][1].record(stream)
+        plan.czt_space(yhat, wbuf, nblk)
+        ev[i][2].record(stream)
+        og.interpolate(wbuf, wstar, nblk)
+        ev[i][3].record(stream)
+        og.apply(wbuf, out, nblk)
+        ev[i][4].record(stream)
+    torch.cuda.synchronize()
+    names = ["czt_time", "czt_space", "interp", "interp_and_stage2"]
+    kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
+    kern_ms["offgrid_stage2"] = kern_ms["interp_and_stage2"] - kern_ms["interp"]
+
+    y_host = torch.from_numpy(d["y"]).pin_memory()
+    out_host = torch.empty((nblk, ndir, N), dtype=torch.complex64).pin_memory()
+    e2e_t = []
+    for i in range(min(args.steps, 200) + 3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y.copy_(y_host, non_blocking=True)
+        og.execute(y, out, nblk)
+        out_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 3:
+            e2e_t.append(time.perf_counter() - t0)
+
+    peaks, peak_kind = load_peaks()
+    fp32 = measure_fp32_peak(fb, 0)
+    # The interpolation reads K = 8 beam vectors per direction and writes one: HBM-bound, with the
+    # compulsory bytes w* out + the grid vectors it reads (once each, at most the whole w).
+    rows_read = min(B, ndir * 8)
+    interp_bytes = 8.0 * nblk * L * (rows_read + ndir)
+    ach = interp_bytes / (kern_ms["interp"] / 1e3) / 1e9
+    roofs = {k: roofline(k, info, nblk, kern_ms[k], peaks, peak_kind, fp32) for k in ("czt_time", "czt_space")}
+    roofs["interp"] = {"bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                       "frac": ach / float(peaks["hbm_gbs"]),
+                       "peak_source": f"{peak_kind} hbm_gbs; bytes = grid beam vectors read once + w* written"}
+    sinfo = type("S", (), dict(M=M, N=N, B=ndir, L=L, S_time=info.S_time, P_time=info.P_time, P_space_x=info.P_space_x,
+                               P_gs=info.P_gs, P_rec=info.P_rec, S_rec=info.S_rec, stage2=2))
+    roofs["offgrid_stage2"] = roofline("stage2", sinfo, nblk, kern_ms["offgrid_stage2"], peaks, peak_kind, fp32)
+    dom = max(("czt_time", "czt_space", "interp", "offgrid_stage2"), key=lambda k: kern_ms[k])
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        facs = O.OffGridFactors(pb, dirs[:16])
+        t_fac = time.perf_counter() - t0
+        done, t_exec = 0, 0.0
+        while t_exec < 10.0 or done == 0:
+            t0 = time.perf_counter()
+            O.fbst_offgrid(pb, d["y"][:4], dirs[:16], factors=facs)
+            t_exec += time.perf_counter() - t0
+            done += 1
+        cpu = {"value": done * 4 * 16 * N / t_exec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} x (4 blocks x 16 of {ndir} off-grid directions), FP64 numpy oracle of Sec. VIII-A, "
+                         f"per-plan factors ({t_fac:.1f} s) excluded"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"OG: off-grid beams (Sec. VIII-A), ULA M={M} with {B} grid beams (2x oversampled), "
+                               f"N={N} L={L} fb=0.5, {ndir} off-grid directions from 8 grid beams each, "
+                               f"{nblk} blocks/step, complex64; value counts off-grid beam-samples",
+                   "M": M, "B_grid": B, "N": N, "L": L, "directions": ndir, "nblk_per_gpu": nblk,
+                   "l2": "flushed before every timed step (256 MiB write, untimed)", "parallelism": "replicas x1"},
+        "rel_err_vs_oracle": rel_err,
+        "interpolated_vs_exact_offgrid_beam": interp_vs_exact,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "roofline": dict(roofs[dom], kernel=dom, traffic=None),
+        "kernels_ms": kern_ms,
+        "kernels_roofline": roofs,
+        "e2e": {"value": float(nblk) * ndir * N * len(e2e_t) / sum(e2e_t), "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * ndir * N)},
+        "gpu_launches": 4 * ((nblk + plan.band.max_blocks - 1) // plan.band.max_blocks) * args.steps,
+        "clocks": clocks,
+        "fp32_peak": fp32,
+        "wall_s_timed_region": wall,
+        "offgrid_create_s": t_create,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    og.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_null(args) -> None:
     """Reference arm of C2N: the FP64 oracle of Eq. (14) on one block x 16 beams per step."""
     import oracle as O
@@ -574,12 +733,42 @@ def run_reference_null(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_reference_offgrid(args) -> None:
+    """Reference arm of OG: the FP64 oracle of Sec. VIII-A on one block x 16 off-grid directions per step."""
+    import oracle as O
+    from synth import configs
+    y = configs.config_data("C2", nblk=1)["y"]
+    dirs = np.stack([np.random.default_rng(2026).uniform(-0.98, 0.98, 64), np.zeros(64)], axis=1)[:16]
+    pb = O.make_problem("ula", 256, 1, 512, 1, 256, frac_bw=0.5, epsilon=1.01, delta_rel=1e-3)
+    fac = O.OffGridFactors(pb, dirs)
+    for _ in range(args.warmup):
+        O.fbst_offgrid(pb, y, dirs, factors=fac)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.fbst_offgrid(pb, y, dirs, factors=fac)
+        times.append(time.perf_counter() - t0)
+    value = len(dirs) * 256 * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "OG oracle sample", "M": 256, "B_grid": 512, "N": 256, "directions": 16},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: 1 block x 16 off-grid directions of OG (FP64 numpy oracle of "
+                                       "Sec. VIII-A, per-plan factors excluded)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     if args.workload == "C2N":
         run_reference_null(args)
+        return
+    if args.workload == "OG":
+        run_reference_offgrid(args)
         return
     args.nblk = 1                     # the oracle runs one block per step: generate only that one
     w, gen = workload(args)
@@ -622,7 +811,7 @@ def main() -> None:
     ap.add_argument("--stage2", default="dense_tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--contraction", default="tf32x3", choices=["tf32x3", "fp32"])
+    ap.add_argument("--contraction", default="fp32", choices=["tf32x3", "fp32"])
     ap.add_argument("--rates", default="1e2,3e2,1e3,3e3,1e4,3e4,1e5")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--streams", type=int, default=3)
@@ -642,6 +831,9 @@ def main() -> None:
         return
     if args.workload == "C2N":
         run_null(args)
+        return
+    if args.workload == "OG":
+        run_offgrid(args)
         return
 
     import torch

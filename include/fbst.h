@@ -288,18 +288,63 @@ int fbst_set_shapes(fbst_plan_t p, int time_E, int time_G, int space_E, int spac
 int fbst_get_shapes(fbst_plan_t p, int* shapes4);
 
 /* ---------------------------------------------------------------------------------------------
+ * Off-grid beams (Sec. VIII-A). A direction (u, v) between the grid beams of a plan gets its beam
+ * vector by interpolating the stage-1 vectors w_b of the grid beams around it: a natural cubic
+ * spline in the direction cosine through the K grid beams nearest to u (K/2 on each side of the
+ * interval that holds u, moved inward at the ends of the grid; the paper uses 8), and for a
+ * rectangular array the tensor product of the splines along u and v (K x K grid beams). Then the
+ * off-grid direction's own regularised least-squares beam (Eq. (5)-(7)):
+ *     bhat*_k = F_u (F*_k^H F*_k + delta I)^{-1} w*_k,   w*_k = sum_i c_{k,i} w_{b_i},
+ * applied by Gohberg-Semencul with one FP32 refinement step (Sec. V) from FP64 plan-time spectra
+ * (generators of every A*_k from their closed form, FP64 Levinson). The interpolation weights are
+ * computed on the host in FP64 and rounded once. w*_k approximates the exact F*_k^H y; the distance
+ * between the two is a property of the spline, not an error of this library.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fbst_offgrid_s* fbst_offgrid_t;
+
+/* Build the off-grid beams of `ndir` directions (host array `directions`, [ndir][2] direction
+ * cosines (u, v), |u|, |v| <= 1; v must be 0 for a linear array) for plan `p`, which must belong to
+ * the current device; K (2..16) grid beams per axis enter each interpolation (fewer if the grid
+ * has fewer). Plan-time kernels run on `stream`, which the call synchronises. Device memory, all
+ * through the plan's allocator: 24*ndir*P_gs + 8*max_blocks*ndir*L bytes and small tables. The plan
+ * must outlive the object and the two must not run concurrently (they share the plan's workspace).
+ * FBST_ERR_INVALID for bad arguments, FBST_ERR_OOM / FBST_ERR_CUDA on allocation or launch failure,
+ * FBST_ERR_NUMERIC if a direction's A is not numerically positive definite. */
+int fbst_offgrid_create(fbst_offgrid_t* out, fbst_plan_t p, const double* directions, int ndir, int K,
+                        void* stream);
+
+/* The interpolation alone: w (device, [nblk][B][L], as written by fbst_czt) -> wstar (device,
+ * [nblk][ndir][L]). Asynchronous on `stream`; pointers 16-byte aligned (else FBST_ERR_INVALID). */
+int fbst_offgrid_interpolate(fbst_offgrid_t o, const void* w, void* wstar, int nblk, void* stream);
+
+/* Off-grid beams from the stage-1 output: w (device, [nblk][B][L]) -> bstar (device,
+ * [nblk][ndir][N]), interpolation then the directions' stage 2. Asynchronous on `stream`. */
+int fbst_offgrid_apply(fbst_offgrid_t o, const void* w, void* bstar, int nblk, void* stream);
+
+/* The whole off-grid transform: y (device, [nblk][M][N]) -> bstar (device, [nblk][ndir][N]) with
+ * the plan's stage 1, the interpolation and the directions' stage 2. Asynchronous on `stream`;
+ * errors as fbst_execute. */
+int fbst_offgrid_execute(fbst_offgrid_t o, const void* y, void* bstar, int nblk, void* stream);
+
+/* Resource management; no counterpart in the paper. Free the object's device memory through the
+ * plan's free function (stream-ordered on the plan's stream; work that uses the object must have
+ * finished). NULL is OK. */
+int fbst_offgrid_destroy(fbst_offgrid_t o);
+
+/* ---------------------------------------------------------------------------------------------
  * Beamspace interference nulling (Sec. VIII-B, Eq. (14)). For interferer beams p_1..p_P of a plan's
  * grid, every output beam b of that plan becomes
  *     bhat_b = F_u A_b^{-1} ( w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j} ),   w = F^H y,
- * the paper's G_{p} w_{p} applied as the product of its two factors. By the derivation of Eq. (14)
- * this is the plain transform of the measurements after each interferer's regularised projection
- * y - F_p (F_p^H F_p + delta I)^{-1} F_p^H y has been subtracted. The nulling object holds, in its
- * own device memory, the cross Gram matrices F_b^H F_{p_j} (B x L x P*L) built from their closed
- * form and the FP64 Gohberg-Semencul spectra of every A_{p_j}^{-1} (from the plan's FP64
- * generators). At run time A_{p_j}^{-1} w_{p_j} is applied in FP64 (A_p has a condition number of
- * about 2/delta_rel, which an FP32 product would pass on to the nulled beams); the contraction with
- * the cross Gram matrices runs on the split-TF32 tensor-core kernel of the dense stage 2 or on its
- * FP32 CUDA-core kernel.
+ * the paper's G_{b,p} w_p with G_{b,p} = F_b^H F_p (F_p^H F_p + delta I)^{-1}. By the derivation of
+ * Eq. (14) this is the plain transform of the measurements after each interferer's regularised
+ * projection y - F_p (F_p^H F_p + delta I)^{-1} F_p^H y has been subtracted. The nulling object
+ * holds, in device memory, every G_{b,p_j} (B x L x P*L complex64), built once in FP64: each row of
+ * F_b^H F_{p_j} from its closed form (exact integer phase reduction), times A_{p_j}^{-1} by the
+ * FP64 Gohberg-Semencul apply with the plan's FP64 generators, rounded once. (Applying the two
+ * factors at run time would pass A_{p_j}^{-1} w_{p_j} through FP32, and A_p's condition number,
+ * about 2/delta_rel, would reach the nulled beams.) At run time the contraction of G with the
+ * interferers' stage-1 vectors runs on the split-TF32 tensor-core kernel of the dense stage 2 or on
+ * its FP32 CUDA-core kernel.
  * ------------------------------------------------------------------------------------------- */
 typedef struct fbst_null_s* fbst_null_t;
 
@@ -312,8 +357,10 @@ typedef enum {
  * from the host array `interferers`) for plan `p`, on the current device; plan-time kernels run
  * on `stream`, which the call synchronises. The plan must outlive the nulling object, and the two
  * must not run concurrently (they share the plan's workspace and status word). Device memory,
- * all obtained through the plan's allocator (see fbst_plan): 8*B*L*P*L bytes of operator (held once; twice during the call), 32*P*P_gs bytes of spectra,
- * 8*max_blocks*(P*L + B*L) bytes of workspace (8*max_blocks*(B*P*L + B*L) for FBST_NULL_FP32).
+ * all obtained through the plan's allocator (see fbst_plan): 8*B*L*P*L bytes of operator (held
+ * once; twice during the call), 32*P*P_gs bytes of spectra, 8*max_blocks*(P*L + B*L) bytes of
+ * workspace (8*max_blocks*(B*P*L + B*L) for FBST_NULL_FP32). Building G costs B*L*P FP64
+ * Gohberg-Semencul applies (6 FFTs of P_gs each).
  * FBST_ERR_INVALID for bad arguments, FBST_ERR_UNSUPPORTED when P*L is not a multiple of 8 for the
  * tensor-core contraction or the exact phase reductions would leave 64-bit range, FBST_ERR_OOM /
  * FBST_ERR_CUDA on allocation or launch failure, FBST_ERR_NUMERIC if a generator is not usable. */

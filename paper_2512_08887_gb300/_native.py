@@ -89,6 +89,11 @@ SIGNATURES = {
     "fbst_null_destroy": (_I, [_VP]),
     "fbst_fp32_fma_peak": (_I, [_VP, _I, C.POINTER(C.c_double), C.POINTER(C.c_double), _VP]),
     "fbst_set_wait_limit": (_I, [_VP, C.c_uint64]),
+    "fbst_offgrid_create": (_I, [C.POINTER(_VP), _VP, C.POINTER(C.c_double), _I, _I, _VP]),
+    "fbst_offgrid_interpolate": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_offgrid_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_offgrid_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
+    "fbst_offgrid_destroy": (_I, [_VP]),
 }
 NULL_CONTRACTION = {"tf32x3": 0, "fp32": 1}
 
@@ -374,9 +379,11 @@ class Batch:
 
 class Nulling:
     """Beamspace interference nulling of grid beams `interferers` for `plan` (Eq. (14);
-    fbst_null_create / fbst_null_destroy). The plan must outlive this object."""
+    fbst_null_create / fbst_null_destroy). The plan must outlive this object. `contraction`: "fp32"
+    (CUDA cores, the accurate one: the correction is about ten times the nulled result at 20 dB, so
+    its product rounding matters) or "tf32x3" (tensor cores, faster, coarser products)."""
 
-    def __init__(self, plan: Plan, interferers, contraction: str = "tf32x3", stream=None):
+    def __init__(self, plan: Plan, interferers, contraction: str = "fp32", stream=None):
         self._lib = load_library()
         self.plan = plan
         self.interferers = [int(p) for p in interferers]
@@ -401,6 +408,55 @@ class Nulling:
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.fbst_null_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class OffGrid:
+    """Off-grid beams of `directions` ((u, v) direction cosines) by interpolation of the plan's grid
+    beam vectors over K grid beams per axis (Sec. VIII-A; fbst_offgrid_create / _destroy). The plan
+    must outlive this object."""
+
+    def __init__(self, plan: Plan, directions, K: int = 8, stream=None):
+        self._lib = load_library()
+        self.plan = plan
+        dirs = [(float(d[0]), float(d[1]) if len(d) > 1 else 0.0) for d in directions]
+        self.ndir = len(dirs)
+        arr = (C.c_double * (2 * max(1, self.ndir)))(*[x for d in dirs for x in d])
+        h = C.c_void_p()
+        _check(self._lib.fbst_offgrid_create(C.byref(h), plan._h, arr, self.ndir, int(K), _stream(stream)),
+               "fbst_offgrid_create")
+        self._h = h
+
+    def _call(self, name, src, dst, nblk, stream):
+        _check(getattr(self._lib, name)(self._h, _ptr(src), _ptr(dst), int(nblk), _stream(stream)), name)
+
+    def interpolate(self, w, wstar, nblk: int, stream=None) -> None:
+        """w [nblk][B][L] -> interpolated beam vectors [nblk][ndir][L]."""
+        self._call("fbst_offgrid_interpolate", w, wstar, nblk, stream)
+
+    def apply(self, w, bstar, nblk: int, stream=None) -> None:
+        """w [nblk][B][L] -> off-grid beams [nblk][ndir][N]."""
+        self._call("fbst_offgrid_apply", w, bstar, nblk, stream)
+
+    def execute(self, y, bstar, nblk: int, stream=None) -> None:
+        """y [nblk][M][N] -> off-grid beams [nblk][ndir][N]."""
+        self._call("fbst_offgrid_execute", y, bstar, nblk, stream)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fbst_offgrid_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

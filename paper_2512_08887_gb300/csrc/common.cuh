@@ -249,6 +249,11 @@ int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cuda
 // Plan-time builders (plan.cu / dense_tc.cu).
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s);
 int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s);
+// Stage-2 operators of `count` arbitrary directions (dirs_dev: device [count][2] direction cosines
+// (u, v)): Gohberg-Semencul spectra XV [count][2][P_gs], circulant spectra Aspec [count][P_gs] (may
+// be null) and the reconstruction tables of the plan's F_u, all from FP64 (plan.cu).
+int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count, float2* XV, float2* Aspec,
+                              float2* pre_r, float2* qspec_r, float2* post_r, cudaStream_t s);
 // In-place FP64 FFT of `rows` contiguous rows of size P (dir -1 forward, +1 unnormalised inverse).
 int fft64_rows(double2* data, int rows, int P, const double2* tw, int dir, cudaStream_t s);
 }  // namespace fbst

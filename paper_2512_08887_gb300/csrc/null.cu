@@ -2,17 +2,23 @@
 //
 // For interferer beams p_1..p_P of the plan's grid, every output beam b gets the bracket of Eq. (14),
 //   wt_b = w_b - sum_j G_{b,j} w_{p_j},   G_{b,j} = F_b^H F_{p_j} (F_{p_j}^H F_{p_j} + delta I)^{-1},
-// applied as the product of its two factors (beta_j = A_{p_j}^{-1} w_{p_j} first), and then the
-// plan's own stage 2: bhat_b = F_u A_b^{-1} wt_b.
+// and then the plan's own stage 2: bhat_b = F_u A_b^{-1} wt_b.
 //
-// Plan time, from closed forms with exact integer phase reduction:
-//   Q[b][ell][j*L + k] = (F_b^H F_{p_j})[ell, k]           B x L x P*L complex64
-//   XV64[j]            Gohberg-Semencul spectra of A_{p_j}^{-1}  P x 2 x P_gs complex128 (from the
-//                                                           plan's FP64 Levinson generators)
+// G_{b,j} is precomputed at plan time, as the paper's form of Eq. (14) suggests, because it is the
+// well-conditioned object: applying its two factors at run time (beta_j = A_{p_j}^{-1} w_{p_j}
+// first) passes through beta_j, whose components along the small eigenvectors of A_{p_j} are
+// amplified by up to its condition number (~2/delta_rel), so rounding beta_j to FP32 and
+// contracting it with F_b^H F_{p_j} loses about that factor in the bracket. G_{b,j} w_{p_j} has no
+// such intermediate.
+//
+// Plan time, in FP64 with exact integer phase reduction:
+//   XV64[j]   Gohberg-Semencul spectra of A_{p_j}^{-1} (from the plan's FP64 Levinson generators)
+//   Gn[b][ell][j*L + k] = (F_b^H F_{p_j} A_{p_j}^{-1})[ell, k]: row ell of F_b^H F_{p_j} from its
+//             closed form, times A_{p_j}^{-1} by the FP64 Gohberg-Semencul apply (Sec. V), rounded
+//             to complex64 once                                        B x L x P*L complex64
 // Run time, per chunk of at most max_blocks blocks:
-//   k_null_beta    beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 (Gohberg-Semencul circulants), rounded
-//                  and written as the right-hand side rhs[blk][j*L + k] = beta_j[k]
-//   contraction    corr[blk][b][ell] = sum_{j,k} Q[b][ell][j*L + k] rhs[blk][j*L + k]
+//   k_null_gather  rhs[blk][j*L + k] = w[blk][p_j][k] (the interferers' stage-1 vectors)
+//   contraction    corr[blk][b][ell] = sum_{j,k} Gn[b][ell][j*L + k] rhs[blk][j*L + k]
 //                  by the split-TF32 tensor-core kernel of the dense stage 2, reading one shared
 //                  right-hand side for every beam (or by its FP32 CUDA-core kernel, from one copy
 //                  per beam), driven through a plan descriptor whose N is L and whose L is P*L:
@@ -56,32 +62,25 @@ __device__ __forceinline__ int64_t red_2D(int64_t q, int64_t D) {
   return m;
 }
 
-// sin(pi*q/D): exact reduction, then sin(pi - x) = sin(x) = sin(-pi - x) folds the angle into
-// [-pi/2, pi/2], so rounding it to float keeps its relative precision next to the zeros.
-__device__ __forceinline__ float sinpi_exact(int64_t q, int64_t D) {
-  int64_t r = red_2D(q, D);
-  if (2 * r > D) r = D - r;
-  else if (2 * r < -D) r = -D - r;
-  return sinpif((float)((double)r / (double)D));
-}
+// sin(pi*q/D) and exp(i*pi*q/D) after the exact reduction of q modulo 2D, in FP64.
+__device__ __forceinline__ double sinpi_red(int64_t q, int64_t D) { return sinpi((double)red_2D(q, D) / (double)D); }
 
-// exp(i*pi*q/D) after the exact reduction.
-__device__ __forceinline__ float2 expipi_exact(int64_t q, int64_t D) {
-  float s, c;
-  sincospif((float)((double)red_2D(q, D) / (double)D), &s, &c);
-  return make_float2(c, s);
+__device__ __forceinline__ double2 expipi_red(int64_t q, int64_t D) {
+  double s, c;
+  sincospi((double)red_2D(q, D) / (double)D, &s, &c);
+  return make_double2(c, s);
 }
 
 // sum_{m<count} exp(i*theta*m) with theta = pi*Y/D: count when theta = 0 mod 2*pi, else
 // exp(i*theta*(count-1)/2) sin(count*theta/2) / sin(theta/2). Each factor has period 4D in Y, so
 // Y is reduced modulo 4D first; the host checks that count*4D fits in 63 bits.
-__device__ float2 dirichlet_f(int64_t Y, int64_t D, int count) {
+__device__ double2 dirichlet_d(int64_t Y, int64_t D, int count) {
   int64_t y = Y % (4 * D);
   if (y < 0) y += 4 * D;
-  if (y % (2 * D) == 0) return make_float2((float)count, 0.f);
-  const float q = sinpi_exact((int64_t)count * y, 2 * D) / sinpi_exact(y, 2 * D);
-  const float2 ph = expipi_exact((int64_t)(count - 1) * y, 2 * D);
-  return make_float2(ph.x * q, ph.y * q);
+  if (y % (2 * D) == 0) return make_double2((double)count, 0.0);
+  const double q = sinpi_red((int64_t)count * y, 2 * D) / sinpi_red(y, 2 * D);
+  const double2 ph = expipi_red((int64_t)(count - 1) * y, 2 * D);
+  return make_double2(ph.x * q, ph.y * q);
 }
 
 // theta_axis = pi*Y/D for output grid index a and interferer grid index ap along an axis of nb
@@ -92,28 +91,17 @@ __device__ __forceinline__ int64_t axis_Y(const null_consts& c, int a, int ap, i
   return 2 * (2 * c.fq * (int64_t)(a - ap) * c.ed * c.L + c.fp * c.en * (lp * (2 * a - nb) - kp * (2 * ap - nb)));
 }
 
-// T[d + L - 1] = D_N(2*pi*eps*d/L) for d = -(L-1)..L-1 (the time factor, a function of k - ell).
-__global__ void k_null_time(float2* T, null_consts c) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * c.L - 1; i += gridDim.x * blockDim.x)
-    T[i] = dirichlet_f(2 * c.en * (int64_t)(i - (c.L - 1)), c.ed * c.L, c.N);
-}
-
-// Q[b][ell][j*L + k] = (F_b^H F_{p_j})[ell, k]. Grid (x: entries of a row, y: ell, z: b).
-__global__ void k_null_Q(float2* __restrict__ Q, const float2* __restrict__ T, const __grid_constant__ null_consts c) {
-  const int ell = blockIdx.y, b = blockIdx.z, L = c.L, PL = c.P * c.L;
+// (F_b^H F_{p_j})[ell, k] in FP64 from the closed form (see the top of this file).
+__device__ __forceinline__ double2 cross_gram_entry(const null_consts& c, int b, int j, int ell, int k) {
+  const int L = c.L;
   const int64_t rden = 2 * c.fq + c.fp;
   const int a = b / c.by, cy = b % c.by;
-  const int64_t lp = (int64_t)ell + 1 - L / 2;
-  const bool two_axes = c.my > 1 || c.by > 1;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < PL; e += gridDim.x * blockDim.x) {
-    const int j = e / L, k = e - j * L;
-    const int pb = c.ip[j], ap = pb / c.by, cp = pb % c.by;
-    const int64_t kp = (int64_t)k + 1 - L / 2;
-    float2 v = cmul(T[k - ell + L - 1],
-                    dirichlet_f(axis_Y(c, a, ap, c.bx, lp, kp), rden * c.ed * L * c.bx, c.mx));
-    if (two_axes) v = cmul(v, dirichlet_f(axis_Y(c, cy, cp, c.by, lp, kp), rden * c.ed * L * c.by, c.my));
-    Q[((size_t)b * L + ell) * PL + e] = v;
-  }
+  const int pb = c.ip[j], ap = pb / c.by, cp = pb % c.by;
+  const int64_t lp = (int64_t)ell + 1 - L / 2, kp = (int64_t)k + 1 - L / 2;
+  double2 v = cmul(dirichlet_d(2 * c.en * (int64_t)(k - ell), c.ed * L, c.N),
+                   dirichlet_d(axis_Y(c, a, ap, c.bx, lp, kp), rden * c.ed * L * c.bx, c.mx));
+  if (c.my > 1 || c.by > 1) v = cmul(v, dirichlet_d(axis_Y(c, cy, cp, c.by, lp, kp), rden * c.ed * L * c.by, c.my));
+  return v;
 }
 
 // Gohberg-Semencul spectra of the interferers' A_p^{-1} (Sec. V) in FP64, before their forward FFT:
@@ -137,67 +125,73 @@ __global__ void k_null_gs_rows(const double2* __restrict__ x64, double2* __restr
 
 template <int PG> struct gs64_e { static constexpr int value = PG >= 2048 ? 16 : (PG >= 8 ? 8 : 2); };
 
-// beta_j = A_{p_j}^{-1} w[blk][p_j] in FP64 through the circulants of size PG >= 2L - 1 (the
-// explicit inverse would cost O(L^2) and, rounded to FP32, loses about kappa(A) in accuracy), then
-// rounded to complex64 and written `copies` times: rhs[blk][c][j*L + ell] = beta_j[ell] for c <
-// copies (1 for the tensor-core contraction, which reads one right-hand side for all beams; B for
-// the CUDA-core one, which reads one per beam). One CTA per (blk, j).
+// Gn[b][ell][j*L + k] = (F_b^H F_{p_j} A_{p_j}^{-1})[ell, k] in FP64, rounded once. Row ell of a
+// product r A^{-1} with A Hermitian is conj(A^{-1} conj(r)): the row of the cross Gram matrix is
+// conjugated, taken through the FP64 Gohberg-Semencul apply of A_{p_j}^{-1} and conjugated back.
+// One CTA per (ell, b, j).
 template <int PG>
 __global__ void __launch_bounds__(PG / gs64_e<PG>::value)
-k_null_beta(const double2* __restrict__ XV64, const float2* __restrict__ w, float2* __restrict__ rhs,
-            const __grid_constant__ null_consts c, int B, int copies, const double2* __restrict__ tw) {
+k_null_G(const double2* __restrict__ XV64, float2* __restrict__ Gn, const __grid_constant__ null_consts c,
+         const double2* __restrict__ tw) {
   constexpr int E = gs64_e<PG>::value, T = PG / E;
   extern __shared__ double2 sm64[];
-  const int blk = blockIdx.x, j = blockIdx.y, t = threadIdx.x, L = c.L, PL = c.P * c.L;
+  const int ell = blockIdx.x, b = blockIdx.y, j = blockIdx.z, t = threadIdx.x, L = c.L, PL = c.P * c.L;
   const double2* Xj = XV64 + (size_t)j * 2 * PG;
-  const float2* wp = w + ((size_t)blk * B + c.ip[j]) * L;
   double2 v[E], X[E], Vv[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) {
     const int i = t + T * r;
-    const float2 a = i < L ? wp[i] : make_float2(0.f, 0.f);
-    v[r] = make_double2(a.x, a.y);
+    v[r] = i < L ? cconj(cross_gram_entry(c, b, j, ell, i)) : make_double2(0.0, 0.0);
     X[r] = Xj[i];
     Vv[r] = Xj[PG + i];
   }
   gs_apply<PG, E>(v, X, Vv, sm64, tw, t, L);
-  float2 bf[E];
+  float2* row = Gn + ((size_t)b * L + ell) * PL + (size_t)j * L;
 #pragma unroll
-  for (int r = 0; r < E; ++r) bf[r] = make_float2((float)v[r].x, (float)v[r].y);
-  float2* out = rhs + (size_t)blk * copies * PL + (size_t)j * L;
-  for (int b = 0; b < copies; ++b) {
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int i = t + T * r;
-      if (i < L) out[(size_t)b * PL + i] = bf[r];
-    }
+  for (int r = 0; r < E; ++r) {
+    const int i = t + T * r;
+    if (i < L) row[i] = make_float2((float)v[r].x, (float)-v[r].y);
   }
 }
 
 template <int PG>
-int launch_beta_P(const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int copies,
-                  int nb, const double2* tw, cudaStream_t s) {
+int build_G_P(const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, cudaStream_t s) {
   constexpr int E = gs64_e<PG>::value;
   const size_t smem = 2 * sizeof(double2) * fft_smem_elems<double2>(PG);
-  FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_beta<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_null_beta<PG><<<dim3(nb, c.P), PG / E, smem, s>>>(XV64, w, rhs, c, B, copies, tw);
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_G<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_null_G<PG><<<dim3(c.L, B, c.P), PG / E, smem, s>>>(XV64, Gn, c, tw);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
-int launch_beta(int PG, const double2* XV64, const float2* w, float2* rhs, const null_consts& c, int B, int copies,
-                int nb, const double2* tw, cudaStream_t s) {
+int build_G(int PG, const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, cudaStream_t s) {
   switch (PG) {
-    case 16: return launch_beta_P<16>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 32: return launch_beta_P<32>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 64: return launch_beta_P<64>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 128: return launch_beta_P<128>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 256: return launch_beta_P<256>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 512: return launch_beta_P<512>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 1024: return launch_beta_P<1024>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 2048: return launch_beta_P<2048>(XV64, w, rhs, c, B, copies, nb, tw, s);
-    case 4096: return launch_beta_P<4096>(XV64, w, rhs, c, B, copies, nb, tw, s);
+    case 16: return build_G_P<16>(XV64, Gn, c, B, tw, s);
+    case 32: return build_G_P<32>(XV64, Gn, c, B, tw, s);
+    case 64: return build_G_P<64>(XV64, Gn, c, B, tw, s);
+    case 128: return build_G_P<128>(XV64, Gn, c, B, tw, s);
+    case 256: return build_G_P<256>(XV64, Gn, c, B, tw, s);
+    case 512: return build_G_P<512>(XV64, Gn, c, B, tw, s);
+    case 1024: return build_G_P<1024>(XV64, Gn, c, B, tw, s);
+    case 2048: return build_G_P<2048>(XV64, Gn, c, B, tw, s);
+    case 4096: return build_G_P<4096>(XV64, Gn, c, B, tw, s);
     default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+// The contraction's right-hand side: rhs[blk][cp][j*L + k] = w[blk][p_j][k] for cp < copies (1 for
+// the tensor-core contraction, which reads one right-hand side for all beams; B for the CUDA-core
+// one, which reads one per beam), as float4 pairs of complex values (L is even).
+__global__ void k_null_gather(const float4* __restrict__ w, float4* __restrict__ rhs, const __grid_constant__ null_consts c,
+                              int B, int copies, int nb) {
+  const int L2 = c.L / 2, PL2 = c.P * L2;
+  const long long total = (long long)nb * copies * PL2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i % PL2);
+    const long long bc = i / PL2;
+    const int blk = (int)(bc / copies);
+    const int j = e / L2, k = e - j * L2;
+    rhs[i] = w[((size_t)blk * B + c.ip[j]) * L2 + k];
   }
 }
 
@@ -224,9 +218,8 @@ struct fbst_null_s {
   fbst_plan_s* plan;     // the plan whose grid, workspace and stage 2 are used (not owned)
   int P;
   int contraction;       // FBST_NULL_TF32X3 or FBST_NULL_FP32
-  fbst_plan_s shadow;    // descriptor of the Q contraction for the dense stage-2 kernels
-  float2* T;             // [2L - 1] time factor (plan time only)
-  float2* Q;             // [B][L][P*L]; freed once the tensor-core planes are built
+  fbst_plan_s shadow;    // descriptor of the G contraction for the dense stage-2 kernels
+  float2* Q;             // Gn [B][L][P*L] complex64; freed once the tensor-core planes are built
   double2* XV64;         // [P][2][P_gs] Gohberg-Semencul spectra of the interferers, FP64
   float2* rhs;           // [max_blocks][1 or B][P*L] (one copy for the tensor-core contraction)
   float2* corr;          // [max_blocks][B][L]
@@ -235,7 +228,7 @@ struct fbst_null_s {
 
 // The object's blocks go back through the plan's allocator (they are in the plan's registry).
 static void free_null(fbst_null_s* n) {
-  void* ptrs[] = {n->T, n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr};
+  void* ptrs[] = {n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr};
   for (void* q : ptrs) plan_free(n->plan, q);
 }
 
@@ -244,7 +237,12 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   const fbst_info& in = n->plan->info;
   const int L = in.L, B = in.B;
   const bool tc = n->contraction == FBST_NULL_TF32X3;
-  FBST_TRY(launch_beta(in.P_gs, n->XV64, w, n->rhs, n->c, B, tc ? 1 : B, nb, n->plan->tw64, s));
+  {
+    const long long n4 = (long long)nb * (tc ? 1 : B) * n->P * L / 2;
+    k_null_gather<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
+                                                       reinterpret_cast<float4*>(n->rhs), n->c, B, tc ? 1 : B, nb);
+    FBST_CUDA_TRY(cudaGetLastError());
+  }
   n->shadow.wait_ns = n->plan->wait_ns;   // the plan's wait limit applies to the contraction too
   const int r = tc ? launch_dense_tc_shared_rhs(&n->shadow, n->rhs, n->corr, nb, s)
                    : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
@@ -322,7 +320,6 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
   const int maxb = p->band.max_blocks;
   int r = FBST_OK;
   do {
-    if ((r = plan_alloc_n(p, &n->T, 2 * (size_t)L - 1)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK)
@@ -330,12 +327,11 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
     if ((r = plan_alloc_n(p, &n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
     // Allocated in stream order on the plan's stream: make the blocks usable on `s`.
     if (cudaStreamSynchronize(p->mem_stream) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
-    k_null_time<<<(2 * L + 254) / 256, 256, 0, s>>>(n->T, c);
-    k_null_Q<<<dim3(std::min((P * L + 255) / 256, 8), L, B), 256, 0, s>>>(n->Q, n->T, c);
     k_null_gs_rows<<<dim3(std::min((in.P_gs + 255) / 256, 16), P), 256, 0, s>>>(p->x64, n->XV64, c, in.P_gs,
                                                                                 p->d_status);
     if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     if ((r = fft64_rows(n->XV64, 2 * P, in.P_gs, p->tw64, -1, s)) != FBST_OK) break;
+    if ((r = build_G(in.P_gs, n->XV64, n->Q, c, B, p->tw64, s)) != FBST_OK) break;
     sh.G = n->Q;
     if (contraction == FBST_NULL_TF32X3) {
       if ((r = build_dense_tc_operand(&sh, s)) != FBST_OK) break;
@@ -348,8 +344,6 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
       r = st;
       break;
     }
-    plan_free(p, n->T);
-    n->T = nullptr;
     if (contraction == FBST_NULL_TF32X3) {
       plan_free(p, n->Q);
       n->Q = nullptr;

@@ -412,6 +412,38 @@ __global__ void k_generators(double2* gen, rat_consts rc, int bx, int by, int mx
   }
 }
 
+// sum_{m<count} exp(-2*pi*i*phi*m) for a real phi (cycles) in FP64: exp(-i*pi*phi*(count-1)) *
+// sin(pi*count*phi) / sin(pi*phi), or count when phi is an integer.
+__device__ double2 dirichlet_real(double phi, int count) {
+  const double den = sinpi(phi);
+  if (den == 0.0) return make_double2((double)count, 0.0);   // every term is 1
+  double s, c;
+  sincospi(-phi * (count - 1), &s, &c);
+  const double q = sinpi(phi * count) / den;
+  return make_double2(c * q, s * q);
+}
+
+// Toeplitz generator of the A of an arbitrary direction (u, v) (Sec. VIII-A: an off-grid beam has
+// its own regularised least-squares problem): as k_generators, with the element sums evaluated in
+// FP64 from the direction cosines (no exact reduction: the phases eps*rho*d*u/L are below 2 cycles,
+// and their FP64 rounding is far below the FP32 results built from them). dirs: [count][2].
+__global__ void k_generators_dir(double2* gen, rat_consts rc, const double* __restrict__ dirs, int mx, int my,
+                                 double delta) {
+  const int k = blockIdx.y;
+  const int L = rc.L;
+  const double eps = (double)rc.en / (double)rc.ed;
+  const double rho = (double)rc.fp / (double)(2 * rc.fq + rc.fp);
+  const double u = dirs[2 * k], v = dirs[2 * k + 1];
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < L; d += gridDim.x * blockDim.x) {
+    const double2 dn = dirichlet_sum(2 * rc.en * d, rc.ed * L, rc.N, +1);
+    double2 af = dirichlet_real(eps * rho * d * u / L, mx);
+    if (my > 1) af = cmul(af, dirichlet_real(eps * rho * d * v / L, my));
+    double2 a = cmul(dn, af);
+    if (d == 0) a.x += delta;
+    gen[(size_t)k * L + d] = a;
+  }
+}
+
 // FP64 Levinson recursion for x = A^{-1} e_0, A Hermitian positive definite Toeplitz with first
 // column c[d] = conj(a(d)). Keeps f_k solving A_k f_k = e_0; with eps_k = sum_{i<k} c[k-i] f_k[i]
 // the extension is f_{k+1}[i] = (f_k[i] - eps_k conj(f_k[k-i])) / (1 - |eps_k|^2) (f_k[k] = 0).
@@ -688,6 +720,55 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
   int st = 0;
   FBST_CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   return st;
+}
+
+int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count, float2* XV, float2* Aspec,
+                              float2* pre_r, float2* qspec_r, float2* post_r, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  const int N = in.N, L = in.L, Pg = in.P_gs;
+  rat_consts rc{in.eps_num, in.eps_den, in.fb_num, in.fb_den, N, L};
+  double2 *gen = nullptr, *x = nullptr, *rows = nullptr, *arows = nullptr, *qrows = nullptr;
+  int r = FBST_OK;
+  do {
+    if ((r = plan_alloc_n(p, &gen, (size_t)count * L)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &x, (size_t)count * L)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &rows, (size_t)count * 2 * Pg)) != FBST_OK) break;
+    if (Aspec && (r = plan_alloc_n(p, &arows, (size_t)count * Pg)) != FBST_OK) break;
+    if ((r = plan_alloc_n(p, &qrows, (size_t)in.S_rec * in.P_rec)) != FBST_OK) break;
+    const int gx = grid_for(L, 256) > 64 ? 64 : grid_for(L, 256);
+    k_generators_dir<<<dim3(gx, count), 256, 0, s>>>(gen, rc, dirs_dev, p->geom.mx, p->geom.my, in.delta);
+    const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
+    if (cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem) != cudaSuccess) {
+      r = FBST_ERR_CUDA;
+      break;
+    }
+    k_levinson<<<count, 256, lev_smem, s>>>(gen, x, L, p->d_status);
+    k_gs_rows<<<dim3(grid_for(Pg, 256) > 64 ? 64 : grid_for(Pg, 256), count), 256, 0, s>>>(x, rows, L, Pg, p->d_status);
+    if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+    if ((r = fft64_rows(rows, 2 * count, Pg, p->tw64, -1, s)) != FBST_OK) break;
+    k_to_c64<<<grid_for((size_t)count * 2 * Pg, 256), 256, 0, s>>>(rows, XV, (size_t)count * 2 * Pg, 1.0 / Pg);
+    if (Aspec) {
+      k_toeplitz_rows<<<dim3(grid_for(Pg, 256) > 64 ? 64 : grid_for(Pg, 256), count), 256, 0, s>>>(gen, arows, L, Pg);
+      if ((r = fft64_rows(arows, count, Pg, p->tw64, -1, s)) != FBST_OK) break;
+      k_to_c64<<<grid_for((size_t)count * Pg, 256), 256, 0, s>>>(arows, Aspec, (size_t)count * Pg, 1.0 / Pg);
+    }
+    k_rec_tables<<<grid_for(L + N, 256), 256, 0, s>>>(pre_r, post_r, rc, in.S_rec);
+    k_rec_kernel_rows<<<grid_for((size_t)in.S_rec * in.P_rec, 256), 256, 0, s>>>(qrows, rc, in.S_rec, in.P_rec);
+    if ((r = fft64_rows(qrows, in.S_rec, in.P_rec, p->tw64, -1, s)) != FBST_OK) break;
+    k_to_c64<<<grid_for((size_t)in.S_rec * in.P_rec, 256), 256, 0, s>>>(qrows, qspec_r, (size_t)in.S_rec * in.P_rec,
+                                                                       1.0 / in.P_rec);
+    if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
+  } while (0);
+  cudaStreamSynchronize(s);
+  for (double2* q : {gen, x, rows, arows, qrows}) plan_free(p, q);
+  if (r != FBST_OK) return r;
+  int st = 0;
+  FBST_CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    return st;
+  }
+  return FBST_OK;
 }
 
 }  // namespace fbst

@@ -190,6 +190,8 @@ k_dense_fp32(const float2* __restrict__ G, const float2* __restrict__ w, float2*
   __shared__ float2 Ws[16][33];
   const int b = blockIdx.y, n0 = blockIdx.x * 64, blk0 = blockIdx.z * 16;
   const int tid = threadIdx.x, tn = tid & 15, tb = tid >> 4;
+  // Blocked accumulation: each K chunk of 32 sums into part[], which is then added to acc[] (the
+  // rounding error grows with the chunk length plus the number of chunks, not with L).
   float2 acc[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
@@ -208,15 +210,23 @@ k_dense_fp32(const float2* __restrict__ G, const float2* __restrict__ w, float2*
       Ws[row][col] = (blk < nblk && k < L) ? w[((size_t)blk * B + b) * L + k] : make_float2(0.f, 0.f);
     }
     __syncthreads();
+    float2 part[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) part[i] = make_float2(0.f, 0.f);
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
       const float2 wv = Ws[tb][kk];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float2 gv = Gs[tn + 16 * i][kk];
-        acc[i].x = fmaf(gv.x, wv.x, fmaf(-gv.y, wv.y, acc[i].x));
-        acc[i].y = fmaf(gv.x, wv.y, fmaf(gv.y, wv.x, acc[i].y));
+        part[i].x = fmaf(gv.x, wv.x, fmaf(-gv.y, wv.y, part[i].x));
+        part[i].y = fmaf(gv.x, wv.y, fmaf(gv.y, wv.x, part[i].y));
       }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[i].x += part[i].x;
+      acc[i].y += part[i].y;
     }
     __syncthreads();
   }
