@@ -9,7 +9,7 @@ oracle is measured and reported on every run); --stage2 gs_ir1 selects the Gohbe
 dense_fp32 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload ULA1024|C2|C3|C4|C5|C2N|OG] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|OG] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
 stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
@@ -199,18 +199,18 @@ class ClockSampler:
 
 def w_is_stream(args) -> bool:
     """Workloads whose blocks are cut from one continuous record (replicas take later segments)."""
-    return args.workload in ("C2", "ULA1024")
+    return args.workload in ("C2", "ULA1024", "NU1024")
 
 
 def workload(args, first_block: int = 0):
     """The workload's geometry and a generator of its input; a replica's record starts at block
     `first_block` of the stream (linear arrays)."""
     from synth import configs
-    if args.workload in ("C2", "ULA1024"):
+    if args.workload in ("C2", "ULA1024", "NU1024"):
         c = configs.CONFIGS[args.workload]
         nb = args.nblk or c["nblk"]
         return dict(kind="ula", mx=c["mx"], my=1, bx=c["bx"], by=1, N=c["N"], frac_bw=c["frac_bw"], nblk=nb,
-                    name=args.workload), \
+                    name=args.workload, offsets=configs.config_geometry(args.workload).offsets), \
             lambda: configs.config_data(args.workload, nblk=nb, first_block=first_block)["y"]
     if args.workload == "C3":
         nb = args.nblk or configs.CONFIGS["C3"]["nblk"]
@@ -223,7 +223,7 @@ def oracle_sample(w: dict, y: np.ndarray, beams, nblk: int, budget_s: float):
     """Time the FP64 oracle (execute part, per-plan LU excluded) on a bounded sample."""
     import oracle as O
     pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], w["N"], frac_bw=w["frac_bw"],
-                        epsilon=1.01, delta_rel=1e-3)
+                        epsilon=1.01, delta_rel=1e-3, offsets=w.get("offsets"))
     t0 = time.perf_counter()
     fac = O.Stage2Factors(pb, beams)
     t_plan = time.perf_counter() - t0
@@ -776,7 +776,7 @@ def run_reference(args) -> None:
     beams = np.linspace(0, w["bx"] * w["by"] - 1, 16).astype(int)
     import oracle as O
     pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], w["N"], frac_bw=w["frac_bw"],
-                        epsilon=1.01, delta_rel=1e-3)
+                        epsilon=1.01, delta_rel=1e-3, offsets=w.get("offsets"))
     fac = O.Stage2Factors(pb, beams)
     for _ in range(args.warmup):
         O.fbst(pb, y[:1], factors=fac)
@@ -866,8 +866,12 @@ def main() -> None:
     M, B, N = w["mx"] * w["my"], w["bx"] * w["by"], w["N"]
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    positions = None
+    if w.get("offsets") is not None:
+        from synth.planewave import ArrayGeometry, array_positions
+        positions = array_positions(ArrayGeometry(w["kind"], w["mx"], w["my"], w["offsets"]))
     plan = fb.Plan(fb.make_geometry(w["kind"], w["mx"], w["my"], w["bx"], w["by"]), N,
-                   fb.make_band(w["frac_bw"], stage2=args.stage2, max_blocks=nblk))
+                   fb.make_band(w["frac_bw"], stage2=args.stage2, max_blocks=nblk), positions=positions)
     info = plan.info
     y = torch.from_numpy(y_np).to(dev)
     out = torch.empty((nblk, B, N), dtype=torch.complex64, device=dev)
@@ -881,7 +885,7 @@ def main() -> None:
         import oracle as O
         beams = np.unique(np.array([0, 1, 77, B // 4, B // 2, 3 * B // 4, B - 2, B - 1]))
         pb = O.make_problem(w["kind"], w["mx"], w["my"], w["bx"], w["by"], N, frac_bw=info.fb_num / info.fb_den,
-                            epsilon=info.eps_num / info.eps_den, delta=info.delta, L=info.L)
+                            epsilon=info.eps_num / info.eps_den, delta=info.delta, L=info.L, offsets=w.get("offsets"))
         ref = O.fbst(pb, y_np[:2], beams=beams)
         rel_err = O.rel_l2(out[:2].cpu().numpy()[:, beams], ref)
 
@@ -986,6 +990,9 @@ def main() -> None:
         "config": {"workload": f"{w['name']}: {w['kind'].upper()} M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
                                f"{nblk} blocks/step per GPU, complex64",
                    "blocks_of_rank0": [first, last],
+                   "element_positions": ("grid" if w.get("offsets") is None else
+                                         "non-uniform: grid moved by N(0, 0.2^2) half wavelengths (Sec. IX); "
+                                         "stage 1b by type-1 NUFFT"),
                    "M": M, "B": B, "N": N, "L": info.L, "nblk_per_gpu": nblk, "stage2": fb.STAGE2_NAMES[info.stage2],
                    "l2": "flushed before every timed step (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},

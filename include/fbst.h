@@ -140,6 +140,20 @@ typedef void (*fbst_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band,
               void* stream, fbst_alloc_fn alloc, fbst_free_fn free, void* ctx);
 
+/* fbst_plan for a linear array whose elements sit at arbitrary positions (Sec. IX, Eq. (16)):
+ * positions (host, [M][2] doubles, (x, 0) in half wavelengths at f_c + Omega, element m's delay
+ * rho*u*x_m; NULL gives the grid, i.e. fbst_plan). Off the grid only the element sum of stage 1b
+ * changes: it becomes a type-1 non-uniform FFT per frequency (each element spread onto an
+ * oversampled grid of nf = pow2(>= 2B) points with a 9-point "exponential of semicircle" kernel,
+ * an nf-point FFT, division by the kernel's Fourier transform; kernel error about 1e-8, below the
+ * FP32 rounding), and the Toeplitz generators of A_b are direct FP64 sums over the positions.
+ * Stage 1a, the Levinson solves and every stage-2 variant are those of fbst_plan. info.P_space_x
+ * reports nf. Rectangular arrays off the grid are FBST_ERR_UNSUPPORTED (their element sum would be
+ * a two-dimensional transform), and so are nulling and off-grid objects on such a plan; batches
+ * accept it. A position that is not finite, or a nonzero y, is FBST_ERR_INVALID. */
+int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* positions, int M, int N, int B,
+                        const fbst_band* band, void* stream, fbst_alloc_fn alloc, fbst_free_fn free, void* ctx);
+
 /* Whole transform: y (device, [nblk][M][N]) -> bhat (device, [nblk][B][N]). nblk = 0 is a no-op.
  * Blocks are independent contiguous batches of N snapshots (Sec. III-A, streaming paragraph). */
 int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);

@@ -60,6 +60,8 @@ _VP, _I = C.c_void_p, C.c_int
 SIGNATURES = {
     "fbst_derive": (_I, [C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), C.POINTER(Info)]),
     "fbst_plan": (_I, [C.POINTER(_VP), C.POINTER(Geometry), _I, _I, _I, C.POINTER(Band), _VP, _VP, _VP, _VP]),
+    "fbst_plan_positions": (_I, [C.POINTER(_VP), C.POINTER(Geometry), C.POINTER(C.c_double), _I, _I, _I,
+                                 C.POINTER(Band), _VP, _VP, _VP, _VP]),
     "fbst_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_execute_host": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_execute_noalloc": (_I, [_VP, _VP, _VP, _I, _VP]),
@@ -231,9 +233,10 @@ class Plan:
     `allocator`: "torch" (default) takes the plan's device memory from PyTorch's caching
     allocator; None lets the library use cudaMallocAsync; or an Allocator. Its memory is allocated
     and freed in stream order on `stream` (default: the current stream), which must outlive the plan.
+    `positions` (M (x, y) pairs, half wavelengths): a linear array off the grid (Sec. IX).
     """
 
-    def __init__(self, geom: Geometry, N: int, band: Band, stream=None, allocator="torch"):
+    def __init__(self, geom: Geometry, N: int, band: Band, stream=None, allocator="torch", positions=None):
         self._lib = load_library()
         self.geom, self.band = geom, band
         self.M, self.B, self.N = geom.mx * geom.my, geom.bx * geom.by, N
@@ -244,8 +247,17 @@ class Plan:
         self._allocator = allocator                 # keeps the callbacks alive with the plan
         fa, ff = allocator.pointers() if allocator is not None else (None, None)
         h = C.c_void_p()
-        _check(self._lib.fbst_plan(C.byref(h), C.byref(geom), self.M, N, self.B, C.byref(band),
-                                   _stream(stream), fa, ff, None), "fbst_plan")
+        if positions is None:
+            _check(self._lib.fbst_plan(C.byref(h), C.byref(geom), self.M, N, self.B, C.byref(band),
+                                       _stream(stream), fa, ff, None), "fbst_plan")
+        else:
+            # Element positions (M x 2, half wavelengths; a linear array has y = 0): Sec. IX.
+            flat = [float(v) for pair in positions for v in (pair[0], pair[1])]
+            if len(flat) != 2 * self.M:
+                raise ValueError(f"positions must hold {self.M} (x, y) pairs")
+            arr = (C.c_double * len(flat))(*flat)
+            _check(self._lib.fbst_plan_positions(C.byref(h), C.byref(geom), arr, self.M, N, self.B, C.byref(band),
+                                                 _stream(stream), fa, ff, None), "fbst_plan_positions")
         self._h = h
         self.info = Info()
         _check(self._lib.fbst_plan_info(self._h, C.byref(self.info)), "fbst_plan_info")

@@ -3,7 +3,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <cmath>
 #include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
 
@@ -125,14 +127,30 @@ const char* fbst_status_string(int status) {
 
 const char* fbst_last_error(void) { return g_last_error; }
 
-int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band, void* stream,
-              fbst_alloc_fn alloc, fbst_free_fn free_fn, void* ctx) {
+int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* positions, int M, int N, int B,
+                        const fbst_band* band, void* stream, fbst_alloc_fn alloc, fbst_free_fn free_fn, void* ctx) {
   if (!out) return FBST_ERR_INVALID;
   *out = nullptr;
   if ((alloc == nullptr) != (free_fn == nullptr)) return FBST_ERR_INVALID;
   fbst_info info;
   FBST_TRY(fbst_derive(g, M, N, B, band, &info));
   if (g->kind == FBST_URA && info.P_space_x != info.P_space_y) return FBST_ERR_UNSUPPORTED;
+  // A non-uniform linear array: stage 1b becomes a type-1 NUFFT onto an oversampled grid of
+  // nf >= 2B points (its size replaces the chirp-z size in info.P_space_x).
+  int nu_nf = 0;
+  const int nu_w = 9;
+  if (positions) {
+    if (g->kind != FBST_ULA) return FBST_ERR_UNSUPPORTED;
+    for (int m = 0; m < M; ++m)
+      if (!std::isfinite(positions[2 * m]) || positions[2 * m + 1] != 0.0) return FBST_ERR_INVALID;
+    nu_nf = 16;
+    while (nu_nf < 2 * B) nu_nf <<= 1;
+    if (nu_nf > kMaxFFT) return FBST_ERR_UNSUPPORTED;
+    const size_t c64 = sizeof(float2), L = info.L;
+    info.table_bytes -= c64 * L * ((size_t)g->mx + info.P_space_x + g->bx);
+    info.table_bytes += sizeof(double) * M + (sizeof(int) + sizeof(float) * nu_w) * L * M + sizeof(float) * B;
+    info.P_space_x = nu_nf;
+  }
   fbst_plan_s* p = new (std::nothrow) fbst_plan_s();
   if (!p) return FBST_ERR_OOM;
   std::memset(p, 0, sizeof(*p));
@@ -149,6 +167,8 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
   p->free_fn = free_fn;
   p->alloc_ctx = ctx;
   p->mem_stream = s;
+  p->nu_nf = nu_nf;
+  p->nu_w = nu_nf ? nu_w : 0;
   int r = FBST_OK;
   do {
     if (cudaGetDevice(&p->device) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
@@ -168,7 +188,20 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
         p->same_axes = 0;
       }
     }
-    for (int a = 0; a < p->n_axes && r == FBST_OK; ++a) {
+    if (nu_nf) {
+      if ((r = dmalloc(p, &p->pos, (size_t)M)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->nu_j0, (size_t)L * M)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->nu_wt, (size_t)L * M * nu_w)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->nu_deconv, (size_t)B)) != FBST_OK) break;
+      std::vector<double> px(M);
+      for (int m = 0; m < M; ++m) px[m] = positions[2 * m];
+      if (cudaStreamSynchronize(s) != cudaSuccess ||
+          cudaMemcpy(p->pos, px.data(), sizeof(double) * M, cudaMemcpyHostToDevice) != cudaSuccess) {
+        r = FBST_ERR_CUDA;
+        break;
+      }
+    }
+    for (int a = 0; a < (nu_nf ? 0 : p->n_axes) && r == FBST_OK; ++a) {
       fbst_axis_tables& ax = p->ax[a];
       if ((r = dmalloc(p, &ax.pre, (size_t)L * ax.Ma)) != FBST_OK) break;
       if ((r = dmalloc(p, &ax.kspec, (size_t)L * ax.P)) != FBST_OK) break;
@@ -206,6 +239,11 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
   }
   *out = p;
   return FBST_OK;
+}
+
+int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band, void* stream,
+              fbst_alloc_fn alloc, fbst_free_fn free_fn, void* ctx) {
+  return fbst_plan_positions(out, g, nullptr, M, N, B, band, stream, alloc, free_fn, ctx);
 }
 
 int fbst_destroy(fbst_plan_t p) {

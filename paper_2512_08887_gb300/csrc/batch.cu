@@ -65,13 +65,13 @@ static int enqueue_batch(fbst_batch_s* bt, const void* const* y, void* const* bh
       }
     }
   }
-  // ---- spatial chirp-z: linear arrays grouped by (P, E, G); rectangular arrays one by one
+  // ---- spatial chirp-z: linear arrays grouped by (P, E, G); rectangular and non-uniform arrays one by one
   {
     std::map<std::tuple<int, int, int>, std::vector<int>> groups;
     for (int i = 0; i < n; ++i) {
       if (nblk[i] <= 0) continue;
       fbst_plan_s* p = bt->plans[i];
-      if (p->geom.kind != FBST_ULA) {
+      if (p->geom.kind != FBST_ULA || p->nu_nf) {
         FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nblk[i], s));
         ++*launches;
         continue;

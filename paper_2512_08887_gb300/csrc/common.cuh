@@ -129,6 +129,15 @@ struct fbst_plan_s {
   float2* gspec_t;     // [S_time][P_time], scaled by 1/P_time
   float2* post_t;      // [L]
 
+  // Stage 1b of a non-uniform linear array (Sec. IX): element x positions and the type-1 NUFFT
+  // tables (nu_nf = 0 for arrays on the grid, which use the chirp-z tables below).
+  int nu_nf;           // oversampled grid size (power of two >= 2B), = info.P_space_x
+  int nu_w;            // spreading width in grid points
+  double* pos;         // [M] element positions along x, half wavelengths
+  int* nu_j0;          // [L][M] first grid point of each element's kernel
+  float* nu_wt;        // [L][M][nu_w] kernel weights
+  float* nu_deconv;    // [B] 1 / kernel Fourier transform at the beam's mode (and / nu_nf scale)
+
   // Stage 1b: spatial chirp-z per frequency; axis 0 = x (all arrays), axis 1 = y (rectangular).
   fbst_axis_tables ax[2];
   int n_axes;
@@ -249,6 +258,10 @@ int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cuda
 // Plan-time builders (plan.cu / dense_tc.cu).
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s);
 int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s);
+// Non-uniform stage 1b: kernel shape for a width of W grid points, and the deconvolution factors
+// of the plan's beams (plan.cu).
+double nufft_beta(int W);
+int nufft_deconv(fbst_plan_s* p, cudaStream_t s);
 // Stage-2 operators of `count` arbitrary directions (dirs_dev: device [count][2] direction cosines
 // (u, v)): Gohberg-Semencul spectra XV [count][2][P_gs], circulant spectra Aspec [count][P_gs] (may
 // be null) and the reconstruction tables of the plan's F_u, all from FP64 (plan.cu).

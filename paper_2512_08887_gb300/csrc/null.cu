@@ -262,6 +262,7 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
   *out = nullptr;
   if (!p || !interferers || P < 1 || P > kMaxInterferers) return FBST_ERR_INVALID;
   if (contraction != FBST_NULL_TF32X3 && contraction != FBST_NULL_FP32) return FBST_ERR_INVALID;
+  if (p->nu_nf) return FBST_ERR_UNSUPPORTED;   // the cross Gram closed form needs grid positions
   const fbst_info& in = p->info;
   const int L = in.L, B = in.B;
   for (int j = 0; j < P; ++j) {

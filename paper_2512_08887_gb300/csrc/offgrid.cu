@@ -132,6 +132,7 @@ int fbst_offgrid_create(fbst_offgrid_t* out, fbst_plan_t p, const double* direct
   if (!out) return FBST_ERR_INVALID;
   *out = nullptr;
   if (!p || !directions || ndir < 1 || ndir > 65535 || K < 2 || K > kMaxWindow) return FBST_ERR_INVALID;
+  if (p->nu_nf) return FBST_ERR_UNSUPPORTED;   // the off-grid generators use the grid positions
   const fbst_info& in = p->info;
   const fbst_geometry& g = p->geom;
   const bool ura = g.kind == FBST_URA;

@@ -444,6 +444,83 @@ __global__ void k_generators_dir(double2* gen, rat_consts rc, const double* __re
   }
 }
 
+// Toeplitz generator of A_b for a linear array at arbitrary positions p_m (Sec. IX: only the element
+// sum changes off the grid): a_b(d) = D_N(2*pi*eps*d/L) * sum_m exp(-2*pi*i*eps*rho*u_b*p_m*d/L)
+// + delta*[d == 0]. One CTA per beam; warp w owns the d range [w*L/8, (w+1)*L/8) and sums over
+// the elements 32 at a time, lane l taking element m: z_m = exp(-2*pi*i*alpha*p_m) with
+// alpha = eps*rho*u_b/L, z_m^d by repeated products from z_m^{d0} (FP64 sincospi once per element
+// and warp; the products lose about d ulps), then a warp reduction per d.
+__global__ void __launch_bounds__(256) k_generators_positions(double2* gen, rat_consts rc, const double* __restrict__ pos,
+                                                              int M, int B, double delta) {
+  extern __shared__ double2 accg[];  // [L]
+  const int b = blockIdx.x, L = rc.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double eps = (double)rc.en / (double)rc.ed;
+  const double rho = (double)rc.fp / (double)(2 * rc.fq + rc.fp);
+  const double alpha = eps * rho * (-1.0 + 2.0 * b / B) / L;
+  const int d0 = (int)((long long)L * warp / 8), d1 = (int)((long long)L * (warp + 1) / 8);
+  for (int d = d0 + lane; d < d1; d += 32) accg[d] = make_double2(0.0, 0.0);
+  __syncwarp();
+  for (int m0 = 0; m0 < M; m0 += 32) {
+    const int m = m0 + lane;
+    double2 z = make_double2(1.0, 0.0), zp = make_double2(0.0, 0.0);
+    if (m < M) {
+      double sn, cs;
+      sincospi(-2.0 * alpha * pos[m], &sn, &cs);
+      z = make_double2(cs, sn);
+      sincospi(-2.0 * alpha * pos[m] * d0, &sn, &cs);
+      zp = make_double2(cs, sn);                // z^{d0}
+    }
+    for (int d = d0; d < d1; ++d) {
+      double2 v = zp;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0) accg[d] = cadd(accg[d], v);
+      zp = cmul(zp, z);
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < L; d += blockDim.x) {
+    double2 a = cmul(dirichlet_sum(2 * rc.en * d, rc.ed * L, rc.N, +1), accg[d]);
+    if (d == 0) a.x += delta;
+    gen[(size_t)b * L + d] = a;
+  }
+}
+
+// Type-1 NUFFT tables of the non-uniform stage 1b (Sec. IX, Eq. (16)). With u_b = 2(b - B/2)/B the
+// element sum is w_b[ell] = sum_m yhat[m, ell] exp(2*pi*i*(b - B/2)*x_m), x_m = 2*kappa_ell*p_m/B
+// (cycles; kappa_ell = rho*(1/fb + eps*ell'/L)): a type-1 transform of the strengths yhat[., ell] at
+// the points x_m onto the centred modes b - B/2. Each point spreads onto nu_w grid points of the
+// nf-point grid (spacing 1/nf) with the "exponential of semicircle" kernel phi(z) = exp(beta *
+// (sqrt(1 - z^2) - 1)), z = (j - nf*x_m) / (nu_w/2). One thread per (ell, m), FP64, rounded once.
+__global__ void k_nufft_tables(int* __restrict__ j0, float* __restrict__ wt, rat_consts rc, const double* __restrict__ pos,
+                               int M, int B, int nf, int W, double beta) {
+  const int L = rc.L;
+  const double eps = (double)rc.en / (double)rc.ed;
+  const double fbv = (double)rc.fp / (double)rc.fq;
+  const double rho = (double)rc.fp / (double)(2 * rc.fq + rc.fp);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)L * M; i += (long long)gridDim.x * blockDim.x) {
+    const int ell = (int)(i / M), m = (int)(i % M);
+    const double lp = (double)(ell + 1 - L / 2);
+    const double kappa = rho * (1.0 / fbv + eps * lp / L);
+    double g = nf * (2.0 * kappa * pos[m] / B);          // grid coordinate of x_m
+    g -= nf * floor(g / nf);                              // into [0, nf)
+    const double first = ceil(g - 0.5 * W);
+    int jj = (int)first;
+    for (int t = 0; t < W; ++t) {
+      const double z = (first + t - g) / (0.5 * W);
+      const double v = z * z < 1.0 ? exp(beta * (sqrt(1.0 - z * z) - 1.0)) : 0.0;
+      wt[(size_t)i * W + t] = (float)v;
+    }
+    jj %= nf;
+    if (jj < 0) jj += nf;
+    j0[i] = jj;
+  }
+}
+
 // FP64 Levinson recursion for x = A^{-1} e_0, A Hermitian positive definite Toeplitz with first
 // column c[d] = conj(a(d)). Keeps f_k solving A_k f_k = e_0; with eps_k = sum_{i<k} c[k-i] f_k[i]
 // the extension is f_{k+1}[i] = (f_k[i] - eps_k conj(f_k[k-i])) / (1 - |eps_k|^2) (f_k[k] = 0).
@@ -622,6 +699,62 @@ static int grid_for(size_t n, int threads) {
     if (fbst_r_ != FBST_OK) return fbst_r_; \
   } while (0)
 
+// Shape parameter of the spreading kernel for a width of W grid points on a 2x oversampled grid
+// (the choice of Barnett, Magland and af Klinteberg for the "exponential of semicircle" kernel).
+double nufft_beta(int W) { return 2.30 * W; }
+
+// Gauss-Legendre nodes and weights on [-1, 1] (n points, FP64): Newton on P_n from the classic
+// cosine initial guess, P_n and P_n' by the three-term recurrence.
+static void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Deconvolution factors of the non-uniform stage 1b: spreading with psi(s) = phi(2s/W) and an
+// unnormalised inverse-sign FFT of the grid give, at mode k, sum_m c_m exp(2*pi*i*k*x_m) times
+// Psi(k/nf) = integral psi(s) exp(2*pi*i*(k/nf)*s) ds = W * integral_0^1 phi(z) cos(pi*(k/nf)*W*z) dz
+// (phi even), up to the aliasing error the kernel width sets. Beam b reads mode k = b - B/2; its
+// factor 1/Psi is computed here by 200-point Gauss-Legendre quadrature in FP64 and rounded once.
+int nufft_deconv(fbst_plan_s* p, cudaStream_t s) {
+  const int B = p->info.B, W = p->nu_w, nf = p->nu_nf;
+  const double beta = nufft_beta(W);
+  constexpr int kQ = 200;
+  double xq[kQ], wq[kQ];
+  gauss_legendre(kQ, xq, wq);
+  float* host = static_cast<float*>(std::malloc(sizeof(float) * B));
+  if (!host) return FBST_ERR_OOM;
+  for (int b = 0; b < B; ++b) {
+    const double nu = (double)(b - B / 2) / nf;
+    double acc = 0.0;
+    for (int i = 0; i < kQ; ++i) {
+      const double z = 0.5 * (xq[i] + 1.0);              // [0, 1]
+      acc += 0.5 * wq[i] * std::exp(beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0)) * std::cos(M_PI * nu * W * z);
+    }
+    host[b] = (float)(1.0 / (W * acc));
+  }
+  const cudaError_t e = cudaMemcpyAsync(p->nu_deconv, host, sizeof(float) * B, cudaMemcpyHostToDevice, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  std::free(host);
+  FBST_CUDA_TRY(e);
+  FBST_CUDA_TRY(e2);
+  return FBST_OK;
+}
+
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
   const fbst_info& in = p->info;
   const int N = in.N, L = in.L, B = in.B;
@@ -655,8 +788,13 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
     if ((rc_status = fft64_rows(scratch, in.S_time, in.P_time, p->tw64, -1, s)) != FBST_OK) break;
     k_to_c64<<<grid_for((size_t)in.S_time * in.P_time, 256), 256, 0, s>>>(scratch, p->gspec_t, (size_t)in.S_time * in.P_time, 1.0 / in.P_time);
 
-    // Stage 1b tables, one set per distinct axis.
-    for (int a = 0; a < p->n_axes; ++a) {
+    // Stage 1b tables: the NUFFT tables of a non-uniform array, else one chirp-z set per axis.
+    if (p->nu_nf) {
+      k_nufft_tables<<<grid_for((size_t)L * in.M, 256), 256, 0, s>>>(p->nu_j0, p->nu_wt, rc, p->pos, in.M, B,
+                                                                    p->nu_nf, p->nu_w, nufft_beta(p->nu_w));
+      if ((rc_status = nufft_deconv(p, s)) != FBST_OK) break;
+    }
+    for (int a = 0; a < (p->nu_nf ? 0 : p->n_axes); ++a) {
       fbst_axis_tables& ax = p->ax[a];
       k_space_tables<<<dim3(grid_for(ax.Ma + ax.Ba, 256) > 64 ? 64 : grid_for(ax.Ma + ax.Ba, 256), L), 256, 0, s>>>(ax.pre, ax.post, rc, ax.Ma, ax.Ba);
       k_space_kernel_rows<<<dim3(grid_for(ax.P, 256) > 64 ? 64 : grid_for(ax.P, 256), L), 256, 0, s>>>(scratch, rc, ax.Ma, ax.Ba, ax.P);
@@ -666,9 +804,16 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
     if (rc_status != FBST_OK) break;
     FBST_CUDA_TRY(cudaGetLastError());
 
-    // Toeplitz generators and Levinson.
-    k_generators<<<dim3(grid_for(L, 256) > 64 ? 64 : grid_for(L, 256), B), 256, 0, s>>>(
-        gen, rc, p->geom.bx, p->geom.by, p->geom.mx, p->geom.my, in.delta);
+    // Toeplitz generators (closed form on the grid, direct FP64 sums over a non-uniform array's
+    // positions) and Levinson.
+    if (p->nu_nf) {
+      FBST_CUDA_TRY(cudaFuncSetAttribute(k_generators_positions, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(L * sizeof(double2))));
+      k_generators_positions<<<B, 256, L * sizeof(double2), s>>>(gen, rc, p->pos, in.M, B, in.delta);
+    } else {
+      k_generators<<<dim3(grid_for(L, 256) > 64 ? 64 : grid_for(L, 256), B), 256, 0, s>>>(
+          gen, rc, p->geom.bx, p->geom.by, p->geom.mx, p->geom.my, in.delta);
+    }
     const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
     FBST_CUDA_TRY(cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
     k_levinson<<<B, 256, lev_smem, s>>>(gen, p->x64, L, p->d_status);

@@ -95,7 +95,7 @@ int fbst_autotune(fbst_plan_t p, int nblk, void* stream, int* shapes4) {
     p->shape_time = pick;
   }
   // Spatial chirp-z (linear arrays).
-  if (r == FBST_OK && p->geom.kind == FBST_ULA) {
+  if (r == FBST_OK && p->geom.kind == FBST_ULA && !p->nu_nf) {
     fft_shape all[16];
     const int n = space_shapes(in.P_space_x, all, 16);
     float best = FLT_MAX;

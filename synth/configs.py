@@ -10,6 +10,8 @@ C4  64 independent linear arrays, M = 2^U{5..10}, N from {128,256,512,1024}, B=M
 ULA1024 linear array M=1024, N=512, B=1024, fb=0.5 (L=1024); K=8 plane waves, 10 dB; one continuous
     record cut into 64 blocks of 512 snapshots; Q=64 sinusoids per waveform; seed 2024. The large
     array (M = B = 1024) at which the transform's roofline is stated.
+NU1024 the ULA1024 signal on the same array with every element but the first moved by N(0, 0.2^2)
+    half wavelengths along the axis (position seed 11): a non-uniform array (Sec. IX).
 C2N the C2 array and grid with one unit-power source on grid beam 160 and two interferers on grid
     beams 64 and 96 at 20 dB above it, 10 dB SNR, 64 blocks; seed 1005. Workload of the beamspace
     interference nulling (Sec. VIII-B), which removes beams 64 and 96.
@@ -25,7 +27,18 @@ CONFIGS = {
     "C3": dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, K=16, snr_db=10.0, seed=1003, nblk=16),
     "ULA1024": dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, K=8, snr_db=10.0, seed=2024,
                     nblk=64, Q=64),
+    "NU1024": dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, K=8, snr_db=10.0, seed=2024,
+                   nblk=64, Q=64, sigma=0.2, pos_seed=11),
 }
+
+
+def config_geometry(name: str):
+    """The array of a workload: the grid, or for a non-uniform workload the perturbed positions."""
+    from .planewave import ArrayGeometry, perturbed_geometry
+    c = CONFIGS[name]
+    if "sigma" in c:
+        return perturbed_geometry(c["kind"], c["mx"], c["my"], c["sigma"], c["pos_seed"])
+    return ArrayGeometry(c["kind"], c["mx"], c["my"])
 
 
 def config_data(name: str, nblk: int | None = None, Q: int | None = None, first_block: int = 0) -> dict:
@@ -39,7 +52,7 @@ def config_data(name: str, nblk: int | None = None, Q: int | None = None, first_
         c["nblk"] = nblk
     if c["kind"] == "ula":
         d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q,
-                       first_block=first_block)
+                       first_block=first_block, geom=config_geometry(name))
     else:
         d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
     d.update(c)

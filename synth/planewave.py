@@ -150,7 +150,7 @@ def _blocks(record: np.ndarray, N: int, nblk: int) -> np.ndarray:
 
 
 def ula_config(M: int, N: int, nblk: int, frac_bw: float, K: int, snr_db: float | None,
-               seed: int, Q: int = 256, first_block: int = 0) -> dict:
+               seed: int, Q: int = 256, first_block: int = 0, geom: ArrayGeometry | None = None) -> dict:
     """One continuous record of K plane waves on an M-element linear array, cut into nblk blocks.
     With first_block > 0 the record starts first_block*N samples later in the same signal (same
     sources; the noise of that segment comes from its own child seed)."""
@@ -158,7 +158,7 @@ def ula_config(M: int, N: int, nblk: int, frac_bw: float, K: int, snr_db: float 
     rs, rn = (np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(2))
     if first_block:
         rn = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, first_block])))
-    geom = ArrayGeometry("ula", M)
+    geom = ArrayGeometry("ula", M) if geom is None else geom     # `geom` may move the elements (Sec. IX)
     src = draw_sources(rs, K, "ula", Q)
     rec = array_record(geom, src, frac_bw, nblk * N, snr_db, rn, t0=first_block * N)
     return {"geom": geom, "sources": src, "frac_bw": frac_bw, "N": N, "nblk": nblk,
