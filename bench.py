@@ -876,6 +876,11 @@ def main() -> None:
     y = torch.from_numpy(y_np).to(dev)
     out = torch.empty((nblk, B, N), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # Stage-1 launch shapes from the library's autotuner (untimed set-up; cached per shape key).
+    shapes = None
+    if not args.no_tune:
+        from paper_2512_08887_gb300 import autotune
+        shapes = autotune.tune(plan, nblk)
 
     # Accuracy on a sample of beams (rank 0; untimed).
     plan.execute(y, out, nblk)
@@ -990,6 +995,7 @@ def main() -> None:
         "config": {"workload": f"{w['name']}: {w['kind'].upper()} M={M} B={B} N={N} L={info.L} fb={w['frac_bw']}, "
                                f"{nblk} blocks/step per GPU, complex64",
                    "blocks_of_rank0": [first, last],
+                   "stage1_shapes": None if shapes is None else {"time": list(shapes[:2]), "space": list(shapes[2:])},
                    "element_positions": ("grid" if w.get("offsets") is None else
                                          "non-uniform: grid moved by N(0, 0.2^2) half wavelengths (Sec. IX); "
                                          "stage 1b by type-1 NUFFT"),

@@ -245,6 +245,7 @@ class Plan:
                 raise ValueError(f"unknown allocator {allocator!r}")
             allocator = torch_allocator()
         self._allocator = allocator                 # keeps the callbacks alive with the plan
+        self.nonuniform = positions is not None
         fa, ff = allocator.pointers() if allocator is not None else (None, None)
         h = C.c_void_p()
         if positions is None:

@@ -19,7 +19,8 @@ def cache_path(path: str | None = None) -> str:
 
 def _key(plan: Plan, nblk: int) -> str:
     i, g = plan.info, plan.geom
-    return f"k{g.kind}:m{g.mx}x{g.my}:b{g.bx}x{g.by}:N{i.N}:L{i.L}:Pt{i.P_time}:Ps{i.P_space_x}:nb{nblk}"
+    nu = ":nonuniform" if getattr(plan, "nonuniform", False) else ""
+    return f"k{g.kind}:m{g.mx}x{g.my}:b{g.bx}x{g.by}:N{i.N}:L{i.L}:Pt{i.P_time}:Ps{i.P_space_x}:nb{nblk}{nu}"
 
 
 def tune(plan: Plan, nblk: int, path: str | None = None, stream=None) -> tuple:
