@@ -183,6 +183,17 @@ int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nb
  * (FBST_ERR_UNSUPPORTED). */
 int fbst_execute_noalloc(fbst_plan_t p, const void* y, void* bhat, int nblk, void* stream);
 
+/* The transform of a continuous record in contiguous, overlapping blocks (Sec. III-A: batches of
+ * snapshots acquired in sequence may overlap). record (device, [M][T] complex64, sample fastest,
+ * 16-byte aligned): block k is samples [k*hop, k*hop + N) of every sensor, read in place;
+ * (nblk - 1)*hop + N <= T. out (device, [B][nblk*hop]): each block contributes its central hop
+ * output samples [c, c + hop), c = (N - hop)/2, so out[b][k*hop + i] is beam b at record time
+ * c + k*hop + i; 1 <= hop <= N with N - hop even. hop = N gives non-overlapping blocks; a smaller
+ * hop drops the block edges, where the block's Fourier extension fits worst. The blocks' full
+ * outputs pass through plan memory ([max_blocks][B][N], through the plan's allocator on first
+ * use). Asynchronous on `stream`; FBST_ERR_INVALID for sizes outside these rules. */
+int fbst_execute_stream(fbst_plan_t p, const void* record, long long T, int hop, void* out, int nblk, void* stream);
+
 /* Stage 1 alone, the fan chirp-z of Sec. IV (App. B for rectangular arrays):
  * y (device, [nblk][M][N]) -> w (device, [nblk][B][L]), w_b = F_b^H y. */
 int fbst_czt(fbst_plan_t p, const void* y, void* w, int nblk, void* stream);

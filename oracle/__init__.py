@@ -26,6 +26,8 @@ from .fbst_oracle import (  # noqa: F401
     offgrid_terms,
     OffGridFactors,
     fbst_offgrid,
+    stream_blocks,
+    fbst_stream,
     fbst,
     dense_operator,
     cross_gram,

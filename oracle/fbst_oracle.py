@@ -418,6 +418,29 @@ def fbst_offgrid(pb: Problem, y: np.ndarray, directions, factors: OffGridFactors
 
 
 # ----------------------------------------------------------------------------------------------
+# Streaming over contiguous, overlapping blocks (Sec. III-A, streaming remark)
+# ----------------------------------------------------------------------------------------------
+
+def stream_blocks(record: np.ndarray, N: int, hop: int, nblk: int) -> np.ndarray:
+    """Blocks k = 0..nblk-1 of N snapshots starting every `hop` samples of a continuous record
+    (M, T): (nblk, M, N)."""
+    return np.stack([record[:, k * hop:k * hop + N] for k in range(nblk)])
+
+
+def fbst_stream(pb: Problem, record: np.ndarray, hop: int, nblk: int, beams=None,
+                factors: Stage2Factors | None = None) -> np.ndarray:
+    """The beams of a continuous record from overlapping blocks: block k covers samples
+    [k*hop, k*hop + N) and contributes its central `hop` output samples, [c, c + hop) with
+    c = (N - hop)/2, at stream times k*hop + c + i. Returns (nbeams, nblk*hop); stream sample j is
+    the beam at record time c + j."""
+    if (pb.N - hop) % 2 or not 1 <= hop <= pb.N:
+        raise ValueError("hop must be in [1, N] with N - hop even")
+    c = (pb.N - hop) // 2
+    bh = fbst(pb, stream_blocks(record, pb.N, hop, nblk), beams=beams, factors=factors)   # (nblk, nb, N)
+    return np.concatenate([bh[k, :, c:c + hop] for k in range(nblk)], axis=1)
+
+
+# ----------------------------------------------------------------------------------------------
 # Tools used by the pins (not part of the method)
 # ----------------------------------------------------------------------------------------------
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "fbst_null_destroy": (_I, [_VP]),
     "fbst_fp32_fma_peak": (_I, [_VP, _I, C.POINTER(C.c_double), C.POINTER(C.c_double), _VP]),
     "fbst_set_wait_limit": (_I, [_VP, C.c_uint64]),
+    "fbst_execute_stream": (_I, [_VP, _VP, C.c_longlong, _I, _VP, _I, _VP]),
     "fbst_offgrid_create": (_I, [C.POINTER(_VP), _VP, C.POINTER(C.c_double), _I, _I, _VP]),
     "fbst_offgrid_interpolate": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_offgrid_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
@@ -282,6 +283,12 @@ class Plan:
     def execute_noalloc(self, y, bhat, nblk: int, stream=None) -> None:
         """Same as execute, intermediates in the library's static device array (no allocation)."""
         self._call("fbst_execute_noalloc", y, bhat, nblk, stream)
+
+    def execute_stream(self, record, T: int, hop: int, out, nblk: int, stream=None) -> None:
+        """Continuous record [M][T] -> beam streams [B][nblk*hop] from blocks every `hop` samples,
+        each contributing its central hop samples (fbst_execute_stream)."""
+        _check(self._lib.fbst_execute_stream(self._h, _ptr(record), int(T), int(hop), _ptr(out), int(nblk),
+                                             _stream(stream)), "fbst_execute_stream")
 
     def czt(self, y, w, nblk: int, stream=None) -> None:
         """Stage 1: y [nblk][M][N] -> w [nblk][B][L]."""

@@ -54,6 +54,8 @@ struct time_job {      // temporal chirp-z of one plan over nblk blocks
   const float2* post;
   int M, N, L, S, nblk;
   long long first;     // first flattened work item of this job
+  long long ys_m, ys_b;  // elements between the rows of two sensors / the starts of two blocks in y
+                         // (N and M*N for [nblk][M][N]; T and the hop for a continuous record [M][T])
 };
 
 struct space_job {     // spatial chirp-z (linear array) of one plan over nblk blocks
@@ -173,6 +175,8 @@ struct fbst_plan_s {
   cudaStream_t copy_in, copy_out;
   cudaEvent_t pipe_ev[12];
 
+  float2* stream_bhat; // [max_blocks][B][N] block outputs of fbst_execute_stream (first use)
+
   int* d_status;       // device status word (FP64 plan kernels report here)
   // Limit of one pipeline wait of the tensor-core stage-2 kernels, ns (0 = the default, 1 s);
   // a wait that runs out makes the kernel record FBST_ERR_TIMEOUT, drain its copies and return.
@@ -220,6 +224,10 @@ inline void share_allocator(fbst_plan_s* dst, const fbst_plan_s* src) {
 
 // Kernel launchers (each returns an fbst_status). All run on `s`.
 int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk, cudaStream_t s);
+// The temporal chirp-z of nblk blocks read in place from a continuous record [M][T] (sample
+// fastest): block k is samples [k*hop, k*hop + N) of every sensor's row.
+int launch_czt_time_record(const fbst_plan_s* p, const float2* record, long long T, int hop, float2* yhat, int nblk,
+                           cudaStream_t s);
 int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s);
 int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 

@@ -2,7 +2,8 @@
 //   yhat[m, ell] = sum_n y[m, n] exp(-2*pi*i*eps*ell'*n/L),   ell' = ell + 1 - L/2,
 // by Bluestein with the output split into S halves that share one forward transform of size P:
 // premultiply by the chirp, FFT, multiply by the kernel spectrum of half h, inverse FFT, post-
-// multiply (tables from plan.cu). Layout y [blk][M][N] -> yhat [blk][L][M]: a work item is G
+// multiply (tables from plan.cu). Layout y [blk][M][N] (or blocks read in place from a continuous
+// record [M][T], the job's strides) -> yhat [blk][L][M]: a work item is G
 // consecutive elements of one block (one Stockham group each); the transpose goes through shared
 // memory and leaves as G-element runs (32 bytes for G = 4) so global stores fill whole sectors.
 //
@@ -37,7 +38,7 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
     const long long li = it - J.first;
     const int blk = (int)(li / ntile), m0 = (int)(li % ntile) * G;
     const int m = m0 + g;
-    const float2* yrow = J.y + ((size_t)blk * M + (m < M ? m : M - 1)) * N;
+    const float2* yrow = J.y + (size_t)blk * J.ys_b + (size_t)(m < M ? m : M - 1) * J.ys_m;
     float2 v[1][E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -117,7 +118,21 @@ long long time_items(const time_job& j, fft_shape sh, int) {
 
 time_job make_time_job(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk) {
   const fbst_info& in = p->info;
-  return time_job{y, yhat, p->pre_t, p->gspec_t, p->post_t, in.M, in.N, in.L, in.S_time, nblk, 0};
+  return time_job{y, yhat, p->pre_t, p->gspec_t, p->post_t, in.M, in.N, in.L, in.S_time, nblk, 0,
+                  (long long)in.N, (long long)in.M * in.N};
+}
+
+int launch_czt_time_record(const fbst_plan_s* p, const float2* record, long long T, int hop, float2* yhat, int nblk,
+                           cudaStream_t s) {
+  if (nblk <= 0) return FBST_OK;
+  job_list<time_job> jl;
+  jl.n = 1;
+  jl.job[0] = make_time_job(p, record, yhat, nblk);
+  jl.job[0].ys_m = T;
+  jl.job[0].ys_b = hop;
+  const fft_shape sh = time_shape(p);
+  jl.total = time_items(jl.job[0], sh, p->info.P_time);
+  return launch_time_jobs(jl, p->info.P_time, sh, p->info.L / p->info.S_time, p->tw32, s);
 }
 
 int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nblk, cudaStream_t s) {

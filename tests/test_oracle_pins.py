@@ -247,3 +247,30 @@ def test_long_record_delay_and_sum_equals_the_direct_sinc_sum(rng):
         direct = O.delay_and_sum_exact(rec, pos, u, v, 0.4, n_out)
         conv = O.delay_and_sum_exact_record(rec, pos, u, v, 0.4, n_out)
         np.testing.assert_allclose(conv, direct, rtol=0, atol=1e-12 * np.abs(direct).max())
+
+
+def test_stream_of_overlapping_blocks_tracks_a_plane_wave_better():
+    # Sec. III-A's streaming remark: blocks every `hop` samples, each contributing its central hop
+    # output samples. A noise-free plane wave from a grid beam pins the stream's time indexing (sample
+    # j is the beam at record time c + j: one sample off would cost about the whole signal) and the
+    # reason to overlap: dropping the block edges, where the Fourier extension fits worst, halves the
+    # bias relative to non-overlapping blocks (hop = N).
+    M, N, fb, b = 16, 64, 0.5, 5
+    pb = O.make_problem("ula", M, 1, M, 1, N=N, frac_bw=fb, delta_rel=1e-3)
+    rs = np.random.default_rng(4)
+    Q = 64
+    src = Source(pb.directions[b, 0], 0.0, (rs.standard_normal(Q) + 1j * rs.standard_normal(Q)) * np.sqrt(0.5 / Q),
+                 rs.uniform(-0.5, 0.5, Q))
+    T = 64 * 12
+    rec = array_record(ArrayGeometry("ula", M), [src], fb, T, None, None)
+    err = {}
+    for hop in (64, 32):
+        nblk = (T - N) // hop + 1
+        out = O.fbst_stream(pb, rec, hop, nblk, beams=[b])[0]
+        c = (N - hop) // 2
+        err[hop] = O.rel_l2(out, waveform(src, np.arange(c, c + nblk * hop)))
+        shifted = O.rel_l2(out, waveform(src, np.arange(c + 1, c + 1 + nblk * hop)))
+        assert shifted > 0.1 > err[hop]
+    assert err[32] < 0.5 * err[64]
+    with pytest.raises(ValueError):
+        O.fbst_stream(pb, rec, 33, 3)                 # N - hop must be even
