@@ -9,7 +9,7 @@ oracle is measured and reported on every run); --stage2 gs_ir1 selects the Gohbe
 dense_fp32 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|OG] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|OG|STREAM] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
 stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
@@ -704,6 +704,106 @@ def run_offgrid(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_stream(args) -> None:
+    """STREAM: the ULA1024 record (1024 elements, 64 x 512 = 32768 samples) as one continuous stream,
+    cut into blocks of N = 512 every hop = 384 samples (25% overlap, 85 blocks); each block
+    contributes its central 384 output samples; one step = fbst_execute_stream over the record;
+    `value` counts output beam-samples."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload STREAM runs on one GPU (replicas take later records)")
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300 import autotune
+    from paper_2512_08887_gb300.build import build
+    from synth import configs
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    c = configs.CONFIGS["ULA1024"]
+    M, B, N, hop = c["mx"], c["bx"], c["N"], args.hop
+    y = configs.config_data("ULA1024")["y"]                    # [64][M][N] blocks of one record
+    rec_np = np.ascontiguousarray(y.transpose(1, 0, 2).reshape(M, -1))
+    T = rec_np.shape[1]
+    nblk = (T - N) // hop + 1
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    plan = fb.Plan(fb.make_geometry("ula", M), N, fb.make_band(c["frac_bw"], stage2=args.stage2, max_blocks=64))
+    info = plan.info
+    if not args.no_tune:
+        autotune.tune(plan, 64)
+    rec = torch.from_numpy(rec_np).to(dev)
+    out = torch.empty((B, nblk * hop), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan.execute_stream(rec, T, hop, out, nblk)
+    if plan.sync_status() != 0:
+        raise SystemExit("device status word set after the streamed transform")
+    pb = O.make_problem("ula", M, 1, B, 1, N, frac_bw=info.fb_num / info.fb_den, epsilon=info.eps_num / info.eps_den,
+                        delta=info.delta, L=info.L)
+    beams = [0, 300, 511, 1023]
+    k0 = 40                                                    # 3 blocks in the middle of the record
+    ref = O.fbst_stream(pb, rec_np[:, k0 * hop:], hop, 3, beams=beams)
+    got = out.cpu().numpy()[beams][:, k0 * hop:(k0 + 3) * hop]
+    rel_err = O.rel_l2(got, ref)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.execute_stream(rec, T, hop, out, nblk)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plan.execute_stream(rec, T, hop, out, nblk)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    units = float(B) * nblk * hop
+    value = units * args.steps / (sum(step_ms) / 1e3)
+
+    rec_host = torch.from_numpy(rec_np).pin_memory()
+    out_host = torch.empty((B, nblk * hop), dtype=torch.complex64).pin_memory()
+    e2e_t = []
+    for i in range(min(args.steps, 50) + 3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec.copy_(rec_host, non_blocking=True)
+        plan.execute_stream(rec, T, hop, out, nblk)
+        out_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 3:
+            e2e_t.append(time.perf_counter() - t0)
+    peaks, peak_kind = load_peaks()
+    fp32 = measure_fp32_peak(fb, 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 stage 1 + " + fb.STAGE2_NAMES[info.stage2] + " stage 2", "data": "synthetic",
+        "config": {"workload": f"STREAM: ULA M={M} B={B} N={N} L={info.L}, one record of {T} samples in {nblk} "
+                               f"blocks every {hop} samples (overlap {N - hop}), central {hop} samples of each; "
+                               "value counts output beam-samples",
+                   "M": M, "B": B, "N": N, "hop": hop, "T": T, "blocks": nblk,
+                   "l2": "flushed before every timed step (256 MiB write, untimed)", "parallelism": "replicas x1"},
+        "rel_err_vs_oracle": rel_err,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "path_roofline": path_roofline(info, nblk, statistics.mean(step_ms), peaks, fp32),
+        "e2e": {"value": units * len(e2e_t) / sum(e2e_t), "unit": UNIT,
+                "h2d_bytes_per_step": int(8 * M * T), "d2h_bytes_per_step": int(8 * B * nblk * hop)},
+        "gpu_launches": 4 * ((nblk + 63) // 64) * args.steps,
+        "clocks": clocks,
+        "fp32_peak": fp32,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_null(args) -> None:
     """Reference arm of C2N: the FP64 oracle of Eq. (14) on one block x 16 beams per step."""
     import oracle as O
@@ -770,6 +870,10 @@ def run_reference(args) -> None:
     if args.workload == "OG":
         run_reference_offgrid(args)
         return
+    if args.workload == "STREAM":
+        # The streamed transform is the per-block transform of the same array on overlapping blocks;
+        # its oracle sample is the block oracle of ULA1024 (one block x 16 beams per step).
+        args.workload = "ULA1024"
     args.nblk = 1                     # the oracle runs one block per step: generate only that one
     w, gen = workload(args)
     y = gen()
@@ -817,6 +921,7 @@ def main() -> None:
     ap.add_argument("--streams", type=int, default=3)
     ap.add_argument("--mem-budget", type=int, default=8 << 30)
     ap.add_argument("--batch-work", type=float, default=4e6)
+    ap.add_argument("--hop", type=int, default=384)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -834,6 +939,9 @@ def main() -> None:
         return
     if args.workload == "OG":
         run_offgrid(args)
+        return
+    if args.workload == "STREAM":
+        run_stream(args)
         return
 
     import torch

@@ -136,8 +136,8 @@ struct fbst_plan_s {
   int nu_nf;           // oversampled grid size (power of two >= 2B), = info.P_space_x
   int nu_w;            // spreading width in grid points
   double* pos;         // [M] element positions along x, half wavelengths
-  int* nu_j0;          // [L][M] first grid point of each element's kernel
-  float* nu_wt;        // [L][M][nu_w] kernel weights
+  int* nu_off;         // [L][nu_nf + 1] start of each grid point's list in nu_ent
+  int2* nu_ent;        // [L][M * nu_w] (element m, kernel weight as float bits) per grid point, by m
   float* nu_deconv;    // [B] 1 / kernel Fourier transform at the beam's mode (and / nu_nf scale)
 
   // Stage 1b: spatial chirp-z per frequency; axis 0 = x (all arrays), axis 1 = y (rectangular).
