@@ -392,6 +392,17 @@ typedef enum {
 int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction,
                      void* stream);
 
+/* fbst_null_create for interferers at arbitrary directions (Sec. VIII-B: exact alignment of the
+ * interference directions with the grid is not required). directions: host [P][2] direction
+ * cosines (u, v), |u|, |v| <= 1, v = 0 for a linear array. Each interferer's vector w_p is
+ * interpolated from the grid beams' stage-1 vectors as in fbst_offgrid_create (a natural cubic
+ * spline through the K grid beams per axis around the direction, 2 <= K <= 16; Sec. VIII-A), and
+ * G_{b,p} = F_b^H F_p A_p^{-1} uses the direction's own F_p: the cross Gram rows from their closed
+ * form in FP64 and A_p^{-1} from the direction's FP64 Levinson generator. The plan must belong to
+ * the current device. Otherwise as fbst_null_create. */
+int fbst_null_create_directions(fbst_null_t* out, fbst_plan_t p, const double* directions, int P, int K,
+                                int contraction, void* stream);
+
 /* The bracket of Eq. (14) alone: w (device, [nblk][B][L], as fbst_czt writes it) ->
  * wt (device, [nblk][B][L]), wt_b = w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j}. wt may equal w
  * (in place); otherwise the two must not overlap. Asynchronous on `stream`; both pointers 16-byte

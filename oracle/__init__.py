@@ -31,6 +31,9 @@ from .fbst_oracle import (  # noqa: F401
     fbst,
     dense_operator,
     cross_gram,
+    cross_gram_direction,
+    OffGridNullingFactors,
+    fbst_nulled_offgrid,
     NullingFactors,
     fbst_nulled,
     lstsq_augmented,

@@ -251,7 +251,13 @@ def dense_operator(pb: Problem, b: int) -> np.ndarray:
 # ----------------------------------------------------------------------------------------------
 
 def cross_gram(pb: Problem, b: int, p: int) -> np.ndarray:
-    """F_b^H F_p (L x L) for beams b and p by direct sums: the product inside G_p of Eq. (14).
+    """F_b^H F_p for grid beams b and p (see cross_gram_direction)."""
+    return cross_gram_direction(pb, b, pb.directions[p])
+
+
+def cross_gram_direction(pb: Problem, b: int, direction) -> np.ndarray:
+    """F_b^H F_p (L x L) for grid beam b and the direction cosines `direction` of p (on or off the
+    grid) by direct sums: the product inside G_p of Eq. (14).
 
     As in gram(), [F_b]_{(m,n),ell} = c_{b,m} * E[n,ell] * phi_b[ell,m] with the carrier
     c_{b,m} = exp(-2j*pi*tau_{b,m}/fb), so
@@ -259,7 +265,7 @@ def cross_gram(pb: Problem, b: int, p: int) -> np.ndarray:
     For b != p the carriers no longer cancel and the element sum is not a function of k - ell.
     """
     E = F_u(pb)                                                                   # (N, L)
-    tb, tp = pb.tau([b])[0], pb.tau([p])[0]                                       # (M,)
+    tb, tp = pb.tau([b])[0], pb.tau(directions=direction)[0]                      # (M,)
     el = lambda tau: (np.exp(-TWO_PI_J * tau / pb.frac_bw)[None, :]
                       * np.exp(-TWO_PI_J * pb.epsilon * np.multiply.outer(pb.lprime, tau) / pb.L))  # (L, M)
     return (E.conj().T @ E) * (el(tb).conj() @ el(tp).T)
@@ -415,6 +421,43 @@ def fbst_offgrid(pb: Problem, y: np.ndarray, directions, factors: OffGridFactors
     w = np.zeros(y.shape[:-2] + (pb.B, pb.L), dtype=np.complex128)
     w[..., factors.beams, :] = fan_coefficients(pb, y, factors.beams)
     return factors.apply(factors.interpolate(w))
+
+
+class OffGridNullingFactors:
+    """Eq. (14) for interferers at arbitrary directions (Sec. VIII-B: exact alignment with the grid
+    is not required): each interferer's vector w_p is interpolated from the grid beam vectors as in
+    Sec. VIII-A, and G_p = F^H F_p (F_p^H F_p + delta I)^{-1} uses that direction's own F_p."""
+
+    def __init__(self, pb: Problem, directions, beams=None, K: int = 8):
+        self.pb = pb
+        self.out = Stage2Factors(pb, beams)
+        self.intf = OffGridFactors(pb, directions, K)         # interpolation terms and LU of each A_p
+        self.C = [[cross_gram_direction(pb, int(b), d) for d in self.intf.directions] for b in self.out.beams]
+
+    def coefficients(self, w: np.ndarray, w_grid: np.ndarray) -> np.ndarray:
+        """The bracket of Eq. (14): w (nblk, nbeams, L) of the output beams, w_grid (nblk, B, L)
+        every grid beam (the interferers' vectors are interpolated from it)."""
+        w = np.asarray(w, dtype=np.complex128)
+        w_int = self.intf.interpolate(w_grid)                               # (nblk, P, L)
+        out = w.copy()
+        for j, lu in enumerate(self.intf.lu):
+            beta = scipy.linalg.lu_solve(lu, w_int[:, j, :].T).T          # (nblk, L)
+            for i in range(len(self.out.beams)):
+                out[:, i, :] -= beta @ self.C[i][j].T
+        return out
+
+
+def fbst_nulled_offgrid(pb: Problem, y: np.ndarray, directions, beams=None,
+                        factors: OffGridNullingFactors | None = None) -> np.ndarray:
+    """FBST with beamspace nulling of interferers at the given directions (Eq. (14), Sec. VIII-A/B):
+    y (nblk, M, N) -> (nblk, nbeams, N)."""
+    y = np.asarray(y)
+    if y.ndim == 2:
+        y = y[None]
+    if factors is None:
+        factors = OffGridNullingFactors(pb, directions, beams)
+    w_grid = fan_coefficients(pb, y)
+    return factors.out.apply(factors.coefficients(w_grid[:, factors.out.beams], w_grid))
 
 
 # ----------------------------------------------------------------------------------------------

@@ -85,6 +85,7 @@ SIGNATURES = {
     "fbst_set_shapes": (_I, [_VP, _I, _I, _I, _I]),
     "fbst_get_shapes": (_I, [_VP, C.POINTER(_I)]),
     "fbst_null_create": (_I, [C.POINTER(_VP), _VP, C.POINTER(_I), _I, _I, _VP]),
+    "fbst_null_create_directions": (_I, [C.POINTER(_VP), _VP, C.POINTER(C.c_double), _I, _I, _I, _VP]),
     "fbst_null_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_null_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_null_launch_count": (_I, [_VP, _I]),
@@ -403,14 +404,24 @@ class Nulling:
     (CUDA cores, the accurate one: the correction is about ten times the nulled result at 20 dB, so
     its product rounding matters) or "tf32x3" (tensor cores, faster, coarser products)."""
 
-    def __init__(self, plan: Plan, interferers, contraction: str = "fp32", stream=None):
+    def __init__(self, plan: Plan, interferers=None, contraction: str = "fp32", stream=None, directions=None,
+                 K: int = 8):
         self._lib = load_library()
         self.plan = plan
-        self.interferers = [int(p) for p in interferers]
-        arr = (C.c_int * max(1, len(self.interferers)))(*self.interferers)
         h = C.c_void_p()
-        _check(self._lib.fbst_null_create(C.byref(h), plan._h, arr, len(self.interferers),
-                                          NULL_CONTRACTION[contraction], _stream(stream)), "fbst_null_create")
+        if directions is not None:
+            # Off-grid interferers: (u, v) direction cosines, vectors interpolated from K grid beams.
+            dirs = [(float(d[0]), float(d[1]) if len(d) > 1 else 0.0) for d in directions]
+            self.interferers = dirs
+            arr = (C.c_double * (2 * max(1, len(dirs))))(*[x for d in dirs for x in d])
+            _check(self._lib.fbst_null_create_directions(C.byref(h), plan._h, arr, len(dirs), int(K),
+                                                         NULL_CONTRACTION[contraction], _stream(stream)),
+                   "fbst_null_create_directions")
+        else:
+            self.interferers = [int(p) for p in interferers]
+            arr = (C.c_int * max(1, len(self.interferers)))(*self.interferers)
+            _check(self._lib.fbst_null_create(C.byref(h), plan._h, arr, len(self.interferers),
+                                              NULL_CONTRACTION[contraction], _stream(stream)), "fbst_null_create")
         self._h = h
 
     def apply(self, w, wt, nblk: int, stream=None) -> None:

@@ -148,8 +148,7 @@ int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* 
     if (nu_nf > kMaxFFT) return FBST_ERR_UNSUPPORTED;
     const size_t c64 = sizeof(float2), L = info.L;
     info.table_bytes -= c64 * L * ((size_t)g->mx + info.P_space_x + g->bx);
-    info.table_bytes += sizeof(double) * M + sizeof(int) * L * (nu_nf + 1) + sizeof(int2) * L * M * nu_w +
-                        sizeof(float) * B;
+    info.table_bytes += sizeof(double) * M + (sizeof(int) + sizeof(float)) * L * M + sizeof(float) * B;
     info.P_space_x = nu_nf;
   }
   fbst_plan_s* p = new (std::nothrow) fbst_plan_s();
@@ -191,8 +190,8 @@ int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* 
     }
     if (nu_nf) {
       if ((r = dmalloc(p, &p->pos, (size_t)M)) != FBST_OK) break;
-      if ((r = dmalloc(p, &p->nu_off, (size_t)L * (nu_nf + 1))) != FBST_OK) break;
-      if ((r = dmalloc(p, &p->nu_ent, (size_t)L * M * nu_w)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->nu_j0, (size_t)L * M)) != FBST_OK) break;
+      if ((r = dmalloc(p, &p->nu_dg, (size_t)L * M)) != FBST_OK) break;
       if ((r = dmalloc(p, &p->nu_deconv, (size_t)B)) != FBST_OK) break;
       std::vector<double> px(M);
       for (int m = 0; m < M; ++m) px[m] = positions[2 * m];

@@ -136,8 +136,8 @@ struct fbst_plan_s {
   int nu_nf;           // oversampled grid size (power of two >= 2B), = info.P_space_x
   int nu_w;            // spreading width in grid points
   double* pos;         // [M] element positions along x, half wavelengths
-  int* nu_off;         // [L][nu_nf + 1] start of each grid point's list in nu_ent
-  int2* nu_ent;        // [L][M * nu_w] (element m, kernel weight as float bits) per grid point, by m
+  int* nu_j0;          // [L][M] first grid point each element reaches
+  float* nu_dg;        // [L][M] its grid coordinate minus that point, in (nu_w/2 - 1, nu_w/2]
   float* nu_deconv;    // [B] 1 / kernel Fourier transform at the beam's mode (and / nu_nf scale)
 
   // Stage 1b: spatial chirp-z per frequency; axis 0 = x (all arrays), axis 1 = y (rectangular).
@@ -266,6 +266,9 @@ int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cuda
 // Plan-time builders (plan.cu / dense_tc.cu).
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s);
 int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s);
+// FP64 first columns x of A^{-1} for `count` arbitrary directions (dirs_dev: device [count][2]);
+// the status word reports a generator that is not positive definite (plan.cu).
+int build_direction_x(fbst_plan_s* p, const double* dirs_dev, int count, double2* x, cudaStream_t s);
 // Non-uniform stage 1b: kernel shape for a width of W grid points, and the deconvolution factors
 // of the plan's beams (plan.cu).
 double nufft_beta(int W);

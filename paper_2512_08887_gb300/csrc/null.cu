@@ -35,10 +35,12 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "gs.cuh"
 #include "launch_util.cuh"
+#include "spline.cuh"
 
 namespace fbst {
 namespace {
@@ -51,6 +53,8 @@ struct null_consts {
   int N, L, P;
   int mx, my, bx, by;   // element and beam grids (linear array: my = by = 1)
   int ip[kMaxInterferers];
+  int offgrid;          // 1: the interferers are the directions (up, vp), not grid beams ip
+  double up[kMaxInterferers], vp[kMaxInterferers];
 };
 
 // q reduced exactly modulo 2D into [-D, D).
@@ -92,25 +96,48 @@ __device__ __forceinline__ int64_t axis_Y(const null_consts& c, int a, int ap, i
 }
 
 // (F_b^H F_{p_j})[ell, k] in FP64 from the closed form (see the top of this file).
+// sum_{m<count} exp(2*pi*i*phi*m) for a real phi (cycles) in FP64 (the element factor toward an
+// off-grid direction, whose phases are not rational): exp(i*pi*phi*(count-1)) sin(pi*count*phi) /
+// sin(pi*phi), or count when phi is an integer.
+__device__ double2 dirichlet_phi(double phi, int count) {
+  const double den = sinpi(phi);
+  if (den == 0.0) return make_double2((double)count, 0.0);
+  double sn, cs;
+  sincospi(phi * (count - 1), &sn, &cs);
+  const double q = sinpi(phi * count) / den;
+  return make_double2(cs * q, sn * q);
+}
+
 __device__ __forceinline__ double2 cross_gram_entry(const null_consts& c, int b, int j, int ell, int k) {
   const int L = c.L;
   const int64_t rden = 2 * c.fq + c.fp;
   const int a = b / c.by, cy = b % c.by;
-  const int pb = c.ip[j], ap = pb / c.by, cp = pb % c.by;
   const int64_t lp = (int64_t)ell + 1 - L / 2, kp = (int64_t)k + 1 - L / 2;
-  double2 v = cmul(dirichlet_d(2 * c.en * (int64_t)(k - ell), c.ed * L, c.N),
-                   dirichlet_d(axis_Y(c, a, ap, c.bx, lp, kp), rden * c.ed * L * c.bx, c.mx));
-  if (c.my > 1 || c.by > 1) v = cmul(v, dirichlet_d(axis_Y(c, cy, cp, c.by, lp, kp), rden * c.ed * L * c.by, c.my));
+  const double2 tf = dirichlet_d(2 * c.en * (int64_t)(k - ell), c.ed * L, c.N);
+  const bool two = c.my > 1 || c.by > 1;
+  if (c.offgrid) {
+    // theta_axis / (2 pi) = rho [(u_b - u_p)/fb + eps (ell' u_b - k' u_p)/L] in FP64.
+    const double rho = (double)c.fp / (double)rden, fbv = (double)c.fp / (double)c.fq;
+    const double eps = (double)c.en / (double)c.ed;
+    auto phi = [&](double ub, double upj) { return rho * ((ub - upj) / fbv + eps * ((double)lp * ub - (double)kp * upj) / L); };
+    double2 v = cmul(tf, dirichlet_phi(phi(-1.0 + 2.0 * a / c.bx, c.up[j]), c.mx));
+    if (two) v = cmul(v, dirichlet_phi(phi(-1.0 + 2.0 * cy / c.by, c.vp[j]), c.my));
+    return v;
+  }
+  const int pb = c.ip[j], ap = pb / c.by, cp = pb % c.by;
+  double2 v = cmul(tf, dirichlet_d(axis_Y(c, a, ap, c.bx, lp, kp), rden * c.ed * L * c.bx, c.mx));
+  if (two) v = cmul(v, dirichlet_d(axis_Y(c, cy, cp, c.by, lp, kp), rden * c.ed * L * c.by, c.my));
   return v;
 }
 
 // Gohberg-Semencul spectra of the interferers' A_p^{-1} (Sec. V) in FP64, before their forward FFT:
 // row 2j holds x / (sqrt(x_0) P) and row 2j+1 holds Z J conj(x) / (sqrt(x_0) P), both zero-padded
-// to P, with x the plan's FP64 first column of A_{p_j}^{-1}.
+// to P, with x the FP64 first column of A_{p_j}^{-1} (the plan's for a grid beam, the direction's
+// own for an off-grid interferer).
 __global__ void k_null_gs_rows(const double2* __restrict__ x64, double2* __restrict__ rows, null_consts c, int P,
                                int* status) {
   const int j = blockIdx.y, L = c.L;
-  const double2* x = x64 + (size_t)c.ip[j] * L;
+  const double2* x = x64 + (size_t)(c.offgrid ? j : c.ip[j]) * L;   // off grid: the directions' own x
   const double x0 = x[0].x;
   if (!(x0 > 0.0)) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(status, (int)FBST_ERR_NUMERIC);
@@ -195,6 +222,34 @@ __global__ void k_null_gather(const float4* __restrict__ w, float4* __restrict__
   }
 }
 
+// Off-grid interferers: rhs[blk][cp][j*L + k] = sum_{i, jj} cx_j[i] cy_j[jj] w[blk][(fx_j + i)*by + fy_j + jj][k],
+// the interferer's vector interpolated from the grid beam vectors (Sec. VIII-A), float4 pairs.
+__global__ void k_null_interp_rhs(const float4* __restrict__ w, float4* __restrict__ rhs,
+                                  const __grid_constant__ null_consts c, const int2* __restrict__ first,
+                                  const float* __restrict__ wts, int B, int copies, int nb, int Kx, int Ky) {
+  const int L2 = c.L / 2, PL2 = c.P * L2;
+  const long long total = (long long)nb * copies * PL2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i % PL2);
+    const int blk = (int)(i / PL2 / copies);
+    const int j = e / L2, k = e - j * L2;
+    const int2 f0 = first[j];
+    const float* cx = wts + (size_t)j * (Kx + Ky);
+    const float* cy = cx + Kx;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int a = 0; a < Kx; ++a)
+      for (int q = 0; q < Ky; ++q) {
+        const float cw = cx[a] * cy[q];
+        const float4 v = w[((size_t)blk * B + (size_t)(f0.x + a) * c.by + f0.y + q) * L2 + k];
+        acc.x = fmaf(cw, v.x, acc.x);
+        acc.y = fmaf(cw, v.y, acc.y);
+        acc.z = fmaf(cw, v.z, acc.z);
+        acc.w = fmaf(cw, v.w, acc.w);
+      }
+    rhs[i] = acc;
+  }
+}
+
 // wt = w - corr over n4 float4 (two complex values each); wt may be w.
 __global__ void k_null_sub(const float4* w, const float4* __restrict__ corr, float4* wt, long long n4) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
@@ -224,11 +279,15 @@ struct fbst_null_s {
   float2* rhs;           // [max_blocks][1 or B][P*L] (one copy for the tensor-core contraction)
   float2* corr;          // [max_blocks][B][L]
   null_consts c;
+  // Off-grid interferers: interpolation windows and weights of each interferer's vector.
+  int Kx, Ky;
+  int2* ifirst;          // [P]
+  float* iwts;           // [P][Kx + Ky]
 };
 
 // The object's blocks go back through the plan's allocator (they are in the plan's registry).
 static void free_null(fbst_null_s* n) {
-  void* ptrs[] = {n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr};
+  void* ptrs[] = {n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr, n->ifirst, n->iwts};
   for (void* q : ptrs) plan_free(n->plan, q);
 }
 
@@ -239,8 +298,13 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   const bool tc = n->contraction == FBST_NULL_TF32X3;
   {
     const long long n4 = (long long)nb * (tc ? 1 : B) * n->P * L / 2;
-    k_null_gather<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
-                                                       reinterpret_cast<float4*>(n->rhs), n->c, B, tc ? 1 : B, nb);
+    if (n->c.offgrid)
+      k_null_interp_rhs<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
+                                                             reinterpret_cast<float4*>(n->rhs), n->c, n->ifirst,
+                                                             n->iwts, B, tc ? 1 : B, nb, n->Kx, n->Ky);
+    else
+      k_null_gather<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
+                                                         reinterpret_cast<float4*>(n->rhs), n->c, B, tc ? 1 : B, nb);
     FBST_CUDA_TRY(cudaGetLastError());
   }
   n->shadow.wait_ns = n->plan->wait_ns;   // the plan's wait limit applies to the contraction too
@@ -255,20 +319,34 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   return FBST_OK;
 }
 
-extern "C" {
-
-int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction, void* stream) {
+// The nulling object of P interferers: grid beams `interferers`, or directions `dirs` ([P][2]
+// direction cosines, interpolated from K grid beams per axis) when interferers is null.
+static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers, const double* dirs, int K, int P,
+                       int contraction, void* stream) {
   if (!out) return FBST_ERR_INVALID;
   *out = nullptr;
-  if (!p || !interferers || P < 1 || P > kMaxInterferers) return FBST_ERR_INVALID;
+  if (!p || (!interferers && !dirs) || P < 1 || P > kMaxInterferers) return FBST_ERR_INVALID;
   if (contraction != FBST_NULL_TF32X3 && contraction != FBST_NULL_FP32) return FBST_ERR_INVALID;
   if (p->nu_nf) return FBST_ERR_UNSUPPORTED;   // the cross Gram closed form needs grid positions
   const fbst_info& in = p->info;
   const int L = in.L, B = in.B;
-  for (int j = 0; j < P; ++j) {
-    if (interferers[j] < 0 || interferers[j] >= B) return FBST_ERR_INVALID;
-    for (int i = 0; i < j; ++i)
-      if (interferers[i] == interferers[j]) return FBST_ERR_INVALID;
+  const bool ura = p->geom.kind == FBST_URA;
+  if (interferers) {
+    for (int j = 0; j < P; ++j) {
+      if (interferers[j] < 0 || interferers[j] >= B) return FBST_ERR_INVALID;
+      for (int i = 0; i < j; ++i)
+        if (interferers[i] == interferers[j]) return FBST_ERR_INVALID;
+    }
+  } else {
+    if (K < 2 || K > kMaxWindow) return FBST_ERR_INVALID;
+    for (int j = 0; j < P; ++j) {
+      const double u = dirs[2 * j], v = dirs[2 * j + 1];
+      if (!std::isfinite(u) || !std::isfinite(v) || std::fabs(u) > 1.0 || std::fabs(v) > 1.0) return FBST_ERR_INVALID;
+      if (!ura && v != 0.0) return FBST_ERR_INVALID;
+    }
+    int cur = -1;
+    FBST_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != p->device) return FBST_ERR_INVALID;
   }
   // 64-bit headroom of the exact phase reductions: |Y| and count * 4D of every Dirichlet sum.
   {
@@ -303,7 +381,29 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
   c.my = p->geom.my;
   c.bx = p->geom.bx;
   c.by = p->geom.by;
-  for (int j = 0; j < P; ++j) c.ip[j] = interferers[j];
+  c.offgrid = interferers ? 0 : 1;
+  std::vector<int2> ifirst;
+  std::vector<float> iwts;
+  for (int j = 0; j < P; ++j) {
+    if (interferers) {
+      c.ip[j] = interferers[j];
+    } else {
+      c.up[j] = dirs[2 * j];
+      c.vp[j] = dirs[2 * j + 1];
+    }
+  }
+  if (!interferers) {
+    n->Kx = std::min(K, p->geom.bx);
+    n->Ky = ura ? std::min(K, p->geom.by) : 1;
+    ifirst.resize(P);
+    iwts.resize((size_t)P * (n->Kx + n->Ky));
+    for (int j = 0; j < P; ++j) {
+      int fx = 0, fy = 0;
+      interp_terms(p->geom.bx, p->geom.by, ura, dirs[2 * j], dirs[2 * j + 1], n->Kx, n->Ky, &fx, &fy,
+                   &iwts[(size_t)j * (n->Kx + n->Ky)]);
+      ifirst[j] = make_int2(fx, fy);
+    }
+  }
 
   // The contraction's descriptor: the dense stage-2 kernels with N := L and L := P*L.
   fbst_plan_s& sh = n->shadow;
@@ -319,6 +419,8 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int maxb = p->band.max_blocks;
+  double* dirs_dev = nullptr;
+  double2* xdir = nullptr;
   int r = FBST_OK;
   do {
     if ((r = plan_alloc_n(p, &n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
@@ -326,9 +428,26 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
     if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK)
       break;
     if ((r = plan_alloc_n(p, &n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
+    if (!interferers) {
+      if ((r = plan_alloc_n(p, &n->ifirst, (size_t)P)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &n->iwts, iwts.size())) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &dirs_dev, 2 * (size_t)P)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &xdir, (size_t)P * L)) != FBST_OK) break;
+    }
     // Allocated in stream order on the plan's stream: make the blocks usable on `s`.
     if (cudaStreamSynchronize(p->mem_stream) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
-    k_null_gs_rows<<<dim3(std::min((in.P_gs + 255) / 256, 16), P), 256, 0, s>>>(p->x64, n->XV64, c, in.P_gs,
+    const double2* xsrc = p->x64;
+    if (!interferers) {
+      if (cudaMemcpy(n->ifirst, ifirst.data(), sizeof(int2) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(n->iwts, iwts.data(), sizeof(float) * iwts.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(dirs_dev, dirs, sizeof(double) * 2 * P, cudaMemcpyHostToDevice) != cudaSuccess) {
+        r = FBST_ERR_CUDA;
+        break;
+      }
+      if ((r = build_direction_x(p, dirs_dev, P, xdir, s)) != FBST_OK) break;
+      xsrc = xdir;
+    }
+    k_null_gs_rows<<<dim3(std::min((in.P_gs + 255) / 256, 16), P), 256, 0, s>>>(xsrc, n->XV64, c, in.P_gs,
                                                                                 p->d_status);
     if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     if ((r = fft64_rows(n->XV64, 2 * P, in.P_gs, p->tw64, -1, s)) != FBST_OK) break;
@@ -351,14 +470,31 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
       sh.G = nullptr;
     }
   } while (0);
+  cudaStreamSynchronize(s);
+  plan_free(p, dirs_dev);
+  plan_free(p, xdir);
   if (r != FBST_OK) {
-    cudaStreamSynchronize(s);
     free_null(n);
     delete n;
     return r;
   }
   *out = n;
   return FBST_OK;
+}
+
+extern "C" {
+
+int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction, void* stream) {
+  if (out) *out = nullptr;
+  if (!interferers) return FBST_ERR_INVALID;
+  return null_create(out, p, interferers, nullptr, 0, P, contraction, stream);
+}
+
+int fbst_null_create_directions(fbst_null_t* out, fbst_plan_t p, const double* directions, int P, int K,
+                                int contraction, void* stream) {
+  if (out) *out = nullptr;
+  if (!directions) return FBST_ERR_INVALID;
+  return null_create(out, p, nullptr, directions, K, P, contraction, stream);
 }
 
 int fbst_null_apply(fbst_null_t n, const void* w, void* wt, int nblk, void* stream) {

@@ -21,53 +21,10 @@
 
 #include "common.cuh"
 #include "launch_util.cuh"
+#include "spline.cuh"
 
 namespace fbst {
 namespace {
-
-constexpr int kMaxWindow = 16;
-
-// Weights c (n of them) with s(xq) = sum_i c_i f_i for the natural cubic spline s through the
-// points (x_i, f_i), x increasing: cubic between knots, continuous first and second derivatives
-// at the inner knots, zero second derivative at both ends. For each unit data vector e_j the
-// moments M_i = s''(x_i) solve the tridiagonal system
-//   h_{i-1} M_{i-1} + 2 (h_{i-1} + h_i) M_i + h_i M_{i+1} = 6 (d_i - d_{i-1}),  M_0 = M_{n-1} = 0,
-// with d_i = (f_{i+1} - f_i) / h_i (Thomas algorithm), and c_j = s_j(xq).
-void spline_weights(const double* x, int n, double xq, double* c) {
-  if (n == 1) {
-    c[0] = 1.0;
-    return;
-  }
-  double h[kMaxWindow], Mo[kMaxWindow], cp[kMaxWindow], dp[kMaxWindow];
-  for (int i = 0; i + 1 < n; ++i) h[i] = x[i + 1] - x[i];
-  int seg = 0;
-  while (seg + 2 < n && xq >= x[seg + 1]) ++seg;
-  const double a = x[seg + 1] - xq, b = xq - x[seg], hs = h[seg];
-  for (int j = 0; j < n; ++j) {
-    auto f = [j](int i) { return i == j ? 1.0 : 0.0; };
-    for (int i = 0; i < n; ++i) Mo[i] = 0.0;
-    const int m = n - 2;   // inner knots 1..n-2
-    for (int r = 0; r < m; ++r) {
-      const int i = r + 1;
-      const double lo = r > 0 ? h[i - 1] : 0.0, di = 2.0 * (h[i - 1] + h[i]), up = r + 1 < m ? h[i] : 0.0;
-      const double rhs = 6.0 * ((f(i + 1) - f(i)) / h[i] - (f(i) - f(i - 1)) / h[i - 1]);
-      const double den = di - lo * (r > 0 ? cp[r - 1] : 0.0);
-      cp[r] = up / den;
-      dp[r] = (rhs - lo * (r > 0 ? dp[r - 1] : 0.0)) / den;
-    }
-    for (int r = m - 1; r >= 0; --r) Mo[r + 1] = dp[r] - (r + 1 < m ? cp[r] * Mo[r + 2] : 0.0);
-    c[j] = (Mo[seg] * a * a * a + Mo[seg + 1] * b * b * b) / (6.0 * hs) + (f(seg) - Mo[seg] * hs * hs / 6.0) * a / hs +
-           (f(seg + 1) - Mo[seg + 1] * hs * hs / 6.0) * b / hs;
-  }
-}
-
-// First of the K consecutive grid indices (of nb) around the direction cosine c: K/2 on each side
-// of the interval that holds it, moved inward at the ends of the grid.
-int window_first(int nb, double c, int K) {
-  const double coord = (c + 1.0) * nb / 2.0;   // grid index of c
-  const int first = (int)std::floor(coord) - (K / 2 - 1);
-  return std::min(std::max(first, 0), nb - K);
-}
 
 // wstar[blk][k][ell] = sum_{i<Kx, j<Ky} cx[k][i] cy[k][j] w[blk][(ax_k + i)*by + ay_k + j][ell], two
 // complex values (one float4) per thread; grid (ell pairs, direction, block).
@@ -151,20 +108,8 @@ int fbst_offgrid_create(fbst_offgrid_t* out, fbst_plan_t p, const double* direct
   std::vector<float> wts((size_t)ndir * (Kx + Ky));
   std::vector<double> dirs(directions, directions + 2 * (size_t)ndir);
   for (int k = 0; k < ndir; ++k) {
-    double x[kMaxWindow], c[kMaxWindow];
-    const int fx = window_first(g.bx, dirs[2 * k], Kx);
-    for (int i = 0; i < Kx; ++i) x[i] = -1.0 + 2.0 * (fx + i) / g.bx;
-    spline_weights(x, Kx, dirs[2 * k], c);
-    for (int i = 0; i < Kx; ++i) wts[(size_t)k * (Kx + Ky) + i] = (float)c[i];
-    int fy = 0;
-    if (ura) {
-      fy = window_first(g.by, dirs[2 * k + 1], Ky);
-      for (int j = 0; j < Ky; ++j) x[j] = -1.0 + 2.0 * (fy + j) / g.by;
-      spline_weights(x, Ky, dirs[2 * k + 1], c);
-      for (int j = 0; j < Ky; ++j) wts[(size_t)k * (Kx + Ky) + Kx + j] = (float)c[j];
-    } else {
-      wts[(size_t)k * (Kx + Ky) + Kx] = 1.0f;
-    }
+    int fx = 0, fy = 0;
+    interp_terms(g.bx, g.by, ura, dirs[2 * k], dirs[2 * k + 1], Kx, Ky, &fx, &fy, &wts[(size_t)k * (Kx + Ky)]);
     first[k] = make_int2(fx, fy);
   }
 

@@ -493,55 +493,27 @@ __global__ void __launch_bounds__(256) k_generators_positions(double2* gen, rat_
 // Type-1 NUFFT tables of the non-uniform stage 1b (Sec. IX, Eq. (16)). With u_b = 2(b - B/2)/B the
 // element sum is w_b[ell] = sum_m yhat[m, ell] exp(2*pi*i*(b - B/2)*x_m), x_m = 2*kappa_ell*p_m/B
 // (cycles; kappa_ell = rho*(1/fb + eps*ell'/L)): a type-1 transform of the strengths yhat[., ell] at
-// the points x_m onto the centred modes b - B/2. Each point spreads onto W grid points of the
-// nf-point grid (spacing 1/nf) with the "exponential of semicircle" kernel phi(z) = exp(beta *
-// (sqrt(1 - z^2) - 1)), z = (j - nf*x_m) / (W/2). The run-time kernel gathers instead of spreading:
-// for every grid point j, the list of (m, weight) of the points that reach it, in order of m. One
-// CTA per frequency: the points' first grid points and weights in FP64 (shared memory), the counts
-// per grid point, their prefix sums (thread 0), then a stable fill by thread 0.
-__global__ void k_nufft_csr(int* __restrict__ off_out, int2* __restrict__ ent_out, rat_consts rc,
-                            const double* __restrict__ pos, int M, int B, int nf, int W, double beta) {
-  extern __shared__ int smc[];
-  int* cnt = smc;                                          // [nf + 1]
-  int* j0 = cnt + nf + 1;                                  // [M]
-  float* wt = reinterpret_cast<float*>(j0 + M);            // [M][W]
-  const int ell = blockIdx.x, L = rc.L;
+// the points x_m onto the centred modes b - B/2. Each point spreads onto the W grid points
+// j0, ..., j0 + W - 1 (mod nf) of the nf-point grid around its grid coordinate g = nf*x_m with the
+// "exponential of semicircle" kernel phi(z) = exp(beta*(sqrt(1 - z^2) - 1)), z = (j - g)/(W/2). The
+// table keeps j0 and g - j0 per (ell, m), computed in FP64 (g - j0 lies in (W/2 - 1, W/2], so its
+// float keeps about 5e-7 absolute); the run-time kernel evaluates the W weights from it.
+__global__ void k_nufft_tables(int* __restrict__ j0, float* __restrict__ dg, rat_consts rc, const double* __restrict__ pos,
+                               int M, int B, int nf, int W) {
+  const int L = rc.L;
   const double eps = (double)rc.en / (double)rc.ed;
   const double fbv = (double)rc.fp / (double)rc.fq;
   const double rho = (double)rc.fp / (double)(2 * rc.fq + rc.fp);
-  const double kappa = rho * (1.0 / fbv + eps * (double)(ell + 1 - L / 2) / L);
-  for (int j = threadIdx.x; j <= nf; j += blockDim.x) cnt[j] = 0;
-  __syncthreads();
-  for (int m = threadIdx.x; m < M; m += blockDim.x) {
-    double g = nf * (2.0 * kappa * pos[m] / B);            // grid coordinate of x_m
-    g -= nf * floor(g / nf);                               // into [0, nf)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)L * M; i += (long long)gridDim.x * blockDim.x) {
+    const int ell = (int)(i / M), m = (int)(i % M);
+    const double kappa = rho * (1.0 / fbv + eps * (double)(ell + 1 - L / 2) / L);
+    double g = nf * (2.0 * kappa * pos[m] / B);          // grid coordinate of x_m
+    g -= nf * floor(g / nf);                              // into [0, nf)
     const double first = ceil(g - 0.5 * W);
-    for (int t = 0; t < W; ++t) {
-      const double z = (first + t - g) / (0.5 * W);
-      wt[m * W + t] = z * z < 1.0 ? (float)exp(beta * (sqrt(1.0 - z * z) - 1.0)) : 0.f;
-    }
+    dg[i] = (float)(g - first);
     int jj = (int)first % nf;
     if (jj < 0) jj += nf;
-    j0[m] = jj;
-    for (int t = 0; t < W; ++t) atomicAdd(&cnt[(jj + t) & (nf - 1)], 1);
-  }
-  __syncthreads();
-  int* off = off_out + (size_t)ell * (nf + 1);
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int j = 0; j < nf; ++j) {
-      const int c = cnt[j];
-      off[j] = acc;
-      cnt[j] = acc;                                        // now the fill cursor of grid point j
-      acc += c;
-    }
-    off[nf] = acc;
-    int2* ent = ent_out + (size_t)ell * M * W;
-    for (int m = 0; m < M; ++m)
-      for (int t = 0; t < W; ++t) {
-        const int j = (j0[m] + t) & (nf - 1);
-        ent[cnt[j]++] = make_int2(m, __float_as_int(wt[m * W + t]));
-      }
+    j0[i] = jj;
   }
 }
 
@@ -814,11 +786,8 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
 
     // Stage 1b tables: the NUFFT tables of a non-uniform array, else one chirp-z set per axis.
     if (p->nu_nf) {
-      const size_t csr_smem = sizeof(int) * ((size_t)p->nu_nf + 1 + in.M) + sizeof(float) * (size_t)in.M * p->nu_w;
-      if (csr_smem > 227 * 1024) { rc_status = FBST_ERR_UNSUPPORTED; break; }
-      FBST_CUDA_TRY(cudaFuncSetAttribute(k_nufft_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csr_smem));
-      k_nufft_csr<<<L, 256, csr_smem, s>>>(p->nu_off, p->nu_ent, rc, p->pos, in.M, B, p->nu_nf, p->nu_w,
-                                          nufft_beta(p->nu_w));
+      k_nufft_tables<<<grid_for((size_t)L * in.M, 256), 256, 0, s>>>(p->nu_j0, p->nu_dg, rc, p->pos, in.M, B,
+                                                                    p->nu_nf, p->nu_w);
       FBST_CUDA_TRY(cudaGetLastError());
       if ((rc_status = nufft_deconv(p, s)) != FBST_OK) break;
     }
@@ -893,6 +862,26 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
   int st = 0;
   FBST_CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   return st;
+}
+
+int build_direction_x(fbst_plan_s* p, const double* dirs_dev, int count, double2* x, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  const int L = in.L;
+  rat_consts rc{in.eps_num, in.eps_den, in.fb_num, in.fb_den, in.N, L};
+  double2* gen = nullptr;
+  FBST_TRY(plan_alloc_n(p, &gen, (size_t)count * L));
+  const int gx = grid_for(L, 256) > 64 ? 64 : grid_for(L, 256);
+  k_generators_dir<<<dim3(gx, count), 256, 0, s>>>(gen, rc, dirs_dev, p->geom.mx, p->geom.my, in.delta);
+  const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem);
+  if (e == cudaSuccess) {
+    k_levinson<<<count, 256, lev_smem, s>>>(gen, x, L, p->d_status);
+    e = cudaGetLastError();
+  }
+  cudaStreamSynchronize(s);
+  plan_free(p, gen);
+  FBST_CUDA_TRY(e);
+  return FBST_OK;
 }
 
 int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count, float2* XV, float2* Aspec,

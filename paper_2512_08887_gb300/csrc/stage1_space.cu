@@ -265,45 +265,58 @@ static int czt_space_ura_P(const fbst_plan_s* p, const float2* yhat, float2* w, 
 // ---------------------------------------------------------------------------------------------
 // Non-uniform linear array (Sec. IX, Eq. (16)): the element sum of each frequency as a type-1
 // NUFFT (tables from plan.cu). Work item = G consecutive frequencies of one block, one transform
-// group of T = NF/E threads per frequency. Thread t gathers its grid points j = t + T*r straight
-// into the FFT's register layout from the plan's per-frequency lists (element m, kernel weight) of
-// the points that reach j (no atomics, no zeroing), takes the unnormalised inverse-sign FFT of the
-// grid, and reads beam b at mode b - B/2 times its deconvolution factor; the [B][G] tile leaves in
-// G-frequency runs.
+// group of T = NF/E threads per frequency: zero the grid (real and imaginary parts in separate
+// shared arrays, so the atomics of neighbouring points fall on different banks), spread every
+// element's yhat[m, ell] onto its W grid points with shared-memory atomics, the W kernel weights
+// evaluated in FP32 from the point's offset to its first grid point (the table keeps that offset to
+// about 5e-7), take the unnormalised inverse-sign FFT of the grid in registers, and read beam b at
+// mode b - B/2 times its deconvolution factor; the [B][G] tile leaves in G-frequency runs.
 // ---------------------------------------------------------------------------------------------
 template <int NF, int E, int G>
 __global__ void __launch_bounds__(G * (NF / E))
-k_nufft_space(const float2* __restrict__ yhat, float2* __restrict__ w, const int* __restrict__ off,
-              const int2* __restrict__ ent, const float* __restrict__ deconv, const float2* __restrict__ tw, int M,
-              int B, int L, int W, int nblk) {
+k_nufft_space(const float2* __restrict__ yhat, float2* __restrict__ w, const int* __restrict__ j0,
+              const float* __restrict__ dg, const float* __restrict__ deconv, const float2* __restrict__ tw, int M,
+              int B, int L, int W, float beta, int nblk) {
   constexpr int T = NF / E;
   static_assert(T <= 32 || G <= 15, "named barriers 1..15, one per transform group");
   extern __shared__ float2 sm[];
   const int g = threadIdx.x / T, t = threadIdx.x % T;
-  float2* fbuf = sm + g * NF;
+  float2* fbuf = sm + g * NF;                       // the FFT's exchange buffer ...
+  float* gre = reinterpret_cast<float*>(fbuf);      // ... first holds the grid: real parts
+  float* gim = gre + NF;                            //     and imaginary parts
   float2* tile = sm + G * NF;  // [B][G + 1]
+  const float inv_half = 2.0f / W;
   long long it0, it1;
   my_range((long long)((L + G - 1) / G) * nblk, &it0, &it1);
   for (long long it = it0; it < it1; ++it) {
     const int lt = (int)(it / nblk), blk = (int)(it % nblk);
     const int ell0 = lt * G, ell = ell0 + g, ellc = ell < L ? ell : L - 1;
-    const float2* row = yhat + ((size_t)blk * L + ellc) * M;
-    const int* of = off + (size_t)ellc * (NF + 1);
-    const int2* en = ent + (size_t)ellc * M * W;
-    float2 v[1][E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      const int j = t + T * r;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int e = of[j], e1 = of[j + 1]; e < e1; ++e) {
-        const int2 q = en[e];
-        const float k = __int_as_float(q.y);
-        const float2 c = row[q.x];
-        acc.x = fmaf(k, c.x, acc.x);
-        acc.y = fmaf(k, c.y, acc.y);
-      }
-      v[0][r] = acc;
+      gre[t + T * r] = 0.f;
+      gim[t + T * r] = 0.f;
     }
+    fft_sync<T>(1 + g);
+    const float2* row = yhat + ((size_t)blk * L + ellc) * M;
+    const int* jr = j0 + (size_t)ellc * M;
+    const float* dr = dg + (size_t)ellc * M;
+    for (int m = t; m < M; m += T) {
+      const float2 c = row[m];
+      const int jb = jr[m];
+      const float d = dr[m];
+      for (int q = 0; q < W; ++q) {
+        const float z = ((float)q - d) * inv_half;
+        const float k = z * z < 1.f ? expf(beta * (sqrtf(1.f - z * z) - 1.f)) : 0.f;
+        const int j = (jb + q) & (NF - 1);
+        atomicAdd(&gre[j], c.x * k);
+        atomicAdd(&gim[j], c.y * k);
+      }
+    }
+    fft_sync<T>(1 + g);
+    float2 v[1][E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[0][r] = make_float2(gre[t + T * r], gim[t + T * r]);
+    fft_sync<T>(1 + g);
     block_fft<NF, E, 1, +1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -332,8 +345,8 @@ static int run_nufft(const fbst_plan_s* p, const float2* yhat, float2* w, int nb
   FBST_TRY(allow_max_smem(k_nufft_space<NF, E, G>));
   const long long items = (long long)((in.L + G - 1) / G) * nblk;
   const int grid = grid_for_items(items, resident_ctas(k_nufft_space<NF, E, G>, G * T, smem));
-  k_nufft_space<NF, E, G><<<grid, G * T, smem, s>>>(yhat, w, p->nu_off, p->nu_ent, p->nu_deconv, p->tw32, in.M, in.B,
-                                                    in.L, p->nu_w, nblk);
+  k_nufft_space<NF, E, G><<<grid, G * T, smem, s>>>(yhat, w, p->nu_j0, p->nu_dg, p->nu_deconv, p->tw32, in.M, in.B,
+                                                    in.L, p->nu_w, (float)nufft_beta(p->nu_w), nblk);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
