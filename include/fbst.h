@@ -384,7 +384,7 @@ typedef enum {
  * must not run concurrently (they share the plan's workspace and status word). Device memory,
  * all obtained through the plan's allocator (see fbst_plan): 8*B*L*P*L bytes of operator (held
  * once; twice during the call), 32*P*P_gs bytes of spectra, 8*max_blocks*(P*L + B*L) bytes of
- * workspace (8*max_blocks*(B*P*L + B*L) for FBST_NULL_FP32). Building G costs B*L*P FP64
+ * workspace. Building G costs B*L*P FP64
  * Gohberg-Semencul applies (6 FFTs of P_gs each).
  * FBST_ERR_INVALID for bad arguments, FBST_ERR_UNSUPPORTED when P*L is not a multiple of 8 for the
  * tensor-core contraction or the exact phase reductions would leave 64-bit range, FBST_ERR_OOM /

@@ -252,6 +252,10 @@ int space_shapes(int P, fft_shape* out, int cap);
 long long time_items(const time_job& j, fft_shape sh, int P);
 long long space_items(const space_job& j, fft_shape sh, int P);
 int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+// The same kernel with one right-hand side per block shared by every beam (w [nblk][L]) when
+// shared_rhs is set.
+int launch_dense_fp32_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, bool shared_rhs,
+                          cudaStream_t s);
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 // The TF32x3 operator for beams [b0, b0 + nbeam) only (FBST_ERR_UNSUPPORTED for other variants).
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,

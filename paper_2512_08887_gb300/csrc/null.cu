@@ -19,10 +19,10 @@
 // Run time, per chunk of at most max_blocks blocks:
 //   k_null_gather  rhs[blk][j*L + k] = w[blk][p_j][k] (the interferers' stage-1 vectors)
 //   contraction    corr[blk][b][ell] = sum_{j,k} Gn[b][ell][j*L + k] rhs[blk][j*L + k]
-//                  by the split-TF32 tensor-core kernel of the dense stage 2, reading one shared
-//                  right-hand side for every beam (or by its FP32 CUDA-core kernel, from one copy
-//                  per beam), driven through a plan descriptor whose N is L and whose L is P*L:
-//                  the contraction has the shape of the dense stage 2
+//                  by the FP32 CUDA-core kernel of the dense stage 2 or its split-TF32 tensor-core
+//                  kernel, both reading one shared right-hand side for every beam, driven through
+//                  a plan descriptor whose N is L and whose L is P*L: the contraction has the shape
+//                  of the dense stage 2
 //   k_null_sub     wt = w - corr
 //
 // The closed form of the cross Gram matrix: with [F_b]_{(m,n),ell} =
@@ -297,19 +297,20 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   const int L = in.L, B = in.B;
   const bool tc = n->contraction == FBST_NULL_TF32X3;
   {
-    const long long n4 = (long long)nb * (tc ? 1 : B) * n->P * L / 2;
+    // One right-hand side per block, read by every beam's tile of the contraction.
+    const long long n4 = (long long)nb * n->P * L / 2;
     if (n->c.offgrid)
       k_null_interp_rhs<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
                                                              reinterpret_cast<float4*>(n->rhs), n->c, n->ifirst,
-                                                             n->iwts, B, tc ? 1 : B, nb, n->Kx, n->Ky);
+                                                             n->iwts, B, 1, nb, n->Kx, n->Ky);
     else
       k_null_gather<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
-                                                         reinterpret_cast<float4*>(n->rhs), n->c, B, tc ? 1 : B, nb);
+                                                         reinterpret_cast<float4*>(n->rhs), n->c, B, 1, nb);
     FBST_CUDA_TRY(cudaGetLastError());
   }
   n->shadow.wait_ns = n->plan->wait_ns;   // the plan's wait limit applies to the contraction too
   const int r = tc ? launch_dense_tc_shared_rhs(&n->shadow, n->rhs, n->corr, nb, s)
-                   : launch_stage2_dense_fp32(&n->shadow, n->rhs, n->corr, nb, s);
+                   : launch_dense_fp32_rhs(&n->shadow, n->rhs, n->corr, nb, true, s);
   if (r != FBST_OK) return r;
   const long long n4 = (long long)nb * B * L / 2;
   k_null_sub<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(w),
@@ -425,8 +426,7 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
   do {
     if ((r = plan_alloc_n(p, &n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
-    if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * (contraction == FBST_NULL_TF32X3 ? 1 : B) * P * L)) != FBST_OK)
-      break;
+    if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * P * L)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
     if (!interferers) {
       if ((r = plan_alloc_n(p, &n->ifirst, (size_t)P)) != FBST_OK) break;

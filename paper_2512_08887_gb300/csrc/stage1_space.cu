@@ -305,8 +305,10 @@ k_nufft_space(const float2* __restrict__ yhat, float2* __restrict__ w, const int
       const int jb = jr[m];
       const float d = dr[m];
       for (int q = 0; q < W; ++q) {
-        const float z = ((float)q - d) * inv_half;
-        const float k = z * z < 1.f ? expf(beta * (sqrtf(1.f - z * z) - 1.f)) : 0.f;
+        const float z = ((float)q - d) * inv_half, z2 = z * z;
+        // sqrt(1 - z^2) - 1 written as -z^2 / (1 + sqrt(1 - z^2)): no cancellation, so the
+        // exponent keeps its relative precision and the weight about 1e-7 absolute.
+        const float k = z2 < 1.f ? expf(-beta * z2 / (1.f + sqrtf(1.f - z2))) : 0.f;
         const int j = (jb + q) & (NF - 1);
         atomicAdd(&gre[j], c.x * k);
         atomicAdd(&gim[j], c.y * k);

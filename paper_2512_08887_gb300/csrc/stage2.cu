@@ -180,74 +180,92 @@ int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nb
 }
 
 // ---------------------------------------------------------------------------------------------
-// Dense FP32 apply: bhat[blk][b][n] = sum_ell G[b][n][ell] * w[blk][b][ell].
-// CTA tile: 64 samples x 16 blocks of one beam, K-chunks of 32; each thread owns 4 x 1 outputs.
+// Dense FP32 apply: bhat[blk][b][n] = sum_ell G[b][n][ell] * w[blk][b][ell] (w_stride = B), or with
+// one right-hand side per block shared by every beam, w[blk][ell] (w_stride = 0: the nulling
+// contraction). CTA tile: 64 samples x 64 blocks of one beam, K chunks of 32 through shared memory;
+// each thread owns 4 x 4 outputs (samples tn + 16 i, blocks tb + 16 j), so a K step costs 8 shared
+// loads for 16 complex multiply-adds. Each K chunk is summed in FP32 on its own and then added to the
+// running sum (blocked accumulation: the rounding error grows with the chunk length plus the number
+// of chunks, not with L).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_dense_fp32(const float2* __restrict__ G, const float2* __restrict__ w, float2* __restrict__ bhat,
-             int B, int N, int L, int nblk) {
+             int B, int N, int L, int nblk, int w_stride) {
   __shared__ float2 Gs[64][33];
-  __shared__ float2 Ws[16][33];
-  const int b = blockIdx.y, n0 = blockIdx.x * 64, blk0 = blockIdx.z * 16;
+  __shared__ float2 Ws[64][33];
+  const int b = blockIdx.y, n0 = blockIdx.x * 64, blk0 = blockIdx.z * 64;
   const int tid = threadIdx.x, tn = tid & 15, tb = tid >> 4;
-  // Blocked accumulation: each K chunk of 32 sums into part[], which is then added to acc[] (the
-  // rounding error grows with the chunk length plus the number of chunks, not with L).
-  float2 acc[4];
+  float2 acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   const float2* Gb = G + (size_t)b * N * L;
+  const size_t wrow = w_stride ? (size_t)B * L : (size_t)L;   // elements between two blocks' rows
+  const float2* wb = w + (w_stride ? (size_t)b * L : 0);
   for (int k0 = 0; k0 < L; k0 += 32) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int idx = tid + 256 * j, row = idx >> 5, col = idx & 31;
-      const int n = n0 + row, k = k0 + col;
+    for (int q = 0; q < 8; ++q) {
+      const int idx = tid + 256 * q, row = idx >> 5, col = idx & 31;
+      const int n = n0 + row, k = k0 + col, blk = blk0 + row;
       Gs[row][col] = (n < N && k < L) ? Gb[(size_t)n * L + k] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int idx = tid + 256 * j, row = idx >> 5, col = idx & 31;
-      const int blk = blk0 + row, k = k0 + col;
-      Ws[row][col] = (blk < nblk && k < L) ? w[((size_t)blk * B + b) * L + k] : make_float2(0.f, 0.f);
+      Ws[row][col] = (blk < nblk && k < L) ? wb[(size_t)blk * wrow + k] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2 part[4];
+    float2 part[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) part[i] = make_float2(0.f, 0.f);
-#pragma unroll 8
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
-      const float2 wv = Ws[tb][kk];
+      float2 gv[4], wv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float2 gv = Gs[tn + 16 * i][kk];
-        part[i].x = fmaf(gv.x, wv.x, fmaf(-gv.y, wv.y, part[i].x));
-        part[i].y = fmaf(gv.x, wv.y, fmaf(gv.y, wv.x, part[i].y));
+      for (int i = 0; i < 4; ++i) gv[i] = Gs[tn + 16 * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) wv[j] = Ws[tb + 16 * j][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          part[i][j].x = fmaf(gv[i].x, wv[j].x, fmaf(-gv[i].y, wv[j].y, part[i][j].x));
+          part[i][j].y = fmaf(gv[i].x, wv[j].y, fmaf(gv[i].y, wv[j].x, part[i][j].y));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[i][j].x += part[i][j].x;
+        acc[i][j].y += part[i][j].y;
       }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      acc[i].x += part[i].x;
-      acc[i].y += part[i].y;
-    }
     __syncthreads();
   }
-  const int blk = blk0 + tb;
-  if (blk < nblk) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int blk = blk0 + tb + 16 * j;
+    if (blk >= nblk) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int n = n0 + tn + 16 * i;
-      if (n < N) bhat[((size_t)blk * B + b) * N + n] = acc[i];
+      if (n < N) bhat[((size_t)blk * B + b) * N + n] = acc[i][j];
     }
   }
 }
 
-int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+int launch_dense_fp32_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, bool shared_rhs,
+                          cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
   const fbst_info& in = p->info;
-  const dim3 grid((in.N + 63) / 64, in.B, (nblk + 15) / 16);
+  const dim3 grid((in.N + 63) / 64, in.B, (nblk + 63) / 64);
   if (grid.z > 65535 || grid.y > 65535) return FBST_ERR_UNSUPPORTED;
-  k_dense_fp32<<<grid, 256, 0, s>>>(p->G, w, bhat, in.B, in.N, in.L, nblk);
+  k_dense_fp32<<<grid, 256, 0, s>>>(p->G, w, bhat, in.B, in.N, in.L, nblk, shared_rhs ? 0 : 1);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
+}
+
+int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+  return launch_dense_fp32_rhs(p, w, bhat, nblk, false, s);
 }
 
 int stage2_launches(const fbst_plan_s* p) {

@@ -90,3 +90,33 @@ def test_autotune_picks_a_compiled_shape_and_keeps_results(tmp_path):
     assert autotune.tune(plan, 8, path=cache) == tuple(shapes)   # cache hit
     with pytest.raises(fb.FBSTError):
         plan.set_shapes(8, 3, 0, 0)
+
+
+def test_all_64_uneven_arrays_of_the_workload_in_one_batch():
+    # The whole uneven-array workload (64 ULAs, M = 2^U{5..10}, N from 128..1024, B = M, fb in
+    # [0.2, 0.6]): the batch equals the per-plan execution bitwise for every array, and the FP64
+    # oracle agrees on sampled beams of arrays spread over the set (every M and N present).
+    import paper_2512_08887_gb300 as fb
+    insts = configs.c4_instances(count=64)
+    plans = _plans(insts)
+    ys = [torch.from_numpy(d["y"]).cuda() for d in insts]
+    ref = [_nan((1, d["B"], d["N"])) for d in insts]
+    for p, y, r in zip(plans, ys, ref):
+        p.execute(y, r, 1)
+    batch = fb.Batch(plans)
+    outs = [_nan((1, d["B"], d["N"])) for d in insts]
+    batch.execute(ys, outs, [1] * 64)
+    batch.execute(ys, outs, [1] * 64)              # graph replay
+    torch.cuda.synchronize()
+    for k, (o, r) in enumerate(zip(outs, ref)):
+        assert torch.equal(o, r), k
+    picked = {}
+    for k, d in enumerate(insts):
+        picked.setdefault((d["M"], d["N"]), k)
+    for k in sorted(picked.values())[::2]:
+        d, i = insts[k], plans[k].info
+        pb = O.make_problem("ula", d["M"], 1, d["M"], 1, d["N"], frac_bw=i.fb_num / i.fb_den,
+                            epsilon=i.eps_num / i.eps_den, delta=i.delta, L=i.L)
+        beams = np.unique(np.array([0, d["M"] // 2, d["M"] - 1]))
+        assert O.rel_l2(outs[k].cpu().numpy()[:, beams], O.fbst(pb, d["y"], beams=beams)) < 1e-5, (k, d["M"], d["N"])
+    batch.close()
