@@ -75,8 +75,16 @@ def flop_model(info) -> dict:
 
 
 # Tensor-core variants: (planes of G, bytes per element, products per complex term, peak dtype,
-# passes over w: prepared planes = read + write + read; the fused TF32x3 kernel reads w once).
-TC_VARIANTS = {4: (4, 2, 3, "bf16", 3), 5: (2, 4, 1, "tf32", 3), 6: (2, 4, 3, "tf32", 1)}
+# passes over w: prepared planes = read + write + read; the fused TF32x3 kernel reads w once; the
+# fused FP16x3 kernel reads it once more for the block scales). FP16 MMAs run at the BF16 rate.
+TC_VARIANTS = {4: (4, 2, 3, "bf16", 3), 5: (2, 4, 1, "tf32", 3), 6: (2, 4, 3, "tf32", 1), 7: (2, 4, 3, "f16", 2)}
+
+
+def tc_peak_of(peaks: dict, dt: str) -> tuple:
+    """Tensor peak for a variant's MMA type: the measured BF16 figure, halved for TF32 (nominal ratio)."""
+    if dt == "tf32":
+        return float(peaks["bf16_tflops"]) * 0.5, "bf16_tflops x 0.5 (tf32 nominal ratio)"
+    return float(peaks["bf16_tflops"]), "bf16_tflops x 1" + (" (f16 = bf16 nominal rate)" if dt == "f16" else "")
 
 
 def nominal_fp32_peak(sms: int, sm_mhz: float) -> dict:
@@ -103,14 +111,14 @@ def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: st
         npl, esz, terms, dt, wpass = TC_VARIANTS[info.stage2]
         nbytes = float(B) * npl * N * L * esz + wpass * B * L * nblk * 8.0 + B * N * nblk * 8.0
         hbm = float(peaks["hbm_gbs"])
-        tc_peak = float(peaks["bf16_tflops"]) * (1.0 if dt == "bf16" else 0.5)  # nominal 2:1 bf16:tf32
+        tc_peak, tc_src = tc_peak_of(peaks, dt)
         if nbytes / (hbm * 1e9) >= terms * flops / (tc_peak * 1e12):
             ach = nbytes / (ms / 1e3) / 1e9
             return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "peak_source": f"{peak_kind} hbm_gbs; bytes = G planes + w passes + bhat"}
         ach = terms * flops / (ms / 1e3) / 1e12
         return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
-                "peak_source": f"{peak_kind} bf16_tflops x {'1' if dt == 'bf16' else '0.5 (tf32 nominal ratio)'}"}
+                "peak_source": f"{peak_kind} {tc_src}"}
     ach = flops / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
             "peak_source": fp32["source"]}
@@ -124,7 +132,7 @@ def path_roofline(info, nblk: int, ms: float, peaks: dict, fp32: dict) -> dict:
     tc = 0.0
     if info.stage2 in TC_VARIANTS:
         _, _, terms, dt, _ = TC_VARIANTS[info.stage2]
-        tc_peak = float(peaks["bf16_tflops"]) * (1.0 if dt == "bf16" else 0.5)
+        tc_peak, _ = tc_peak_of(peaks, dt)
         tc = terms * fm["stage2"] * nblk / (tc_peak * 1e12)
     else:
         alu += fm["stage2"] * nblk

@@ -63,7 +63,10 @@ enum fbst_stage2_kind {
   FBST_STAGE2_DENSE_FP32 = 3,  /* precomputed G_b = F_u A_b^{-1} (Sec. III-B), FP32 CUDA cores */
   FBST_STAGE2_DENSE_BF16X3 = 4,/* G_b on tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
   FBST_STAGE2_DENSE_TF32 = 5,  /* G_b on tensor cores in TF32, FP32 accumulate */
-  FBST_STAGE2_DENSE_TF32X3 = 6 /* G_b on tensor cores, split TF32 (hi*hi + hi*lo + lo*hi): FP32-class */
+  FBST_STAGE2_DENSE_TF32X3 = 6,/* G_b on tensor cores, split TF32 (hi*hi + hi*lo + lo*hi): FP32-class */
+  FBST_STAGE2_DENSE_F16X3 = 7  /* G_b on tensor cores, split FP16 (hi*hi + hi*lo + lo*hi) with exact
+                                  power-of-two scales per beam of G and per block of w: FP32-class,
+                                  at twice the TF32 MMA rate */
 };
 
 /* Array and beam grid. M = mx*my elements, B = bx*by beams. A linear array has my = by = 1. */

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "FBST_OK", -1: "FBST_ERR_INVALID", -2: "FBST_ERR_OOM", -3: "F
                 -4: "FBST_ERR_UNSUPPORTED", -5: "FBST_ERR_TIMEOUT", -6: "FBST_ERR_NUMERIC"}
 ULA, URA = 0, 1
 STAGE2 = {"auto": 0, "gs": 1, "gs_ir1": 2, "dense_fp32": 3, "dense_bf16x3": 4, "dense_tf32": 5,
-          "dense_tf32x3": 6}
+          "dense_tf32x3": 6, "dense_f16x3": 7}
 STAGE2_NAMES = {v: k for k, v in STAGE2.items()}
 
 

@@ -88,7 +88,8 @@ int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cuda
     case FBST_STAGE2_DENSE_FP32: return launch_stage2_dense_fp32(p, w, bhat, nb, s);
     case FBST_STAGE2_DENSE_BF16X3:
     case FBST_STAGE2_DENSE_TF32:
-    case FBST_STAGE2_DENSE_TF32X3: return launch_stage2_dense_tc(p, w, bhat, nb, s);
+    case FBST_STAGE2_DENSE_TF32X3:
+    case FBST_STAGE2_DENSE_F16X3: return launch_stage2_dense_tc(p, w, bhat, nb, s);
     default: return FBST_ERR_INVALID;
   }
 }
@@ -374,7 +375,8 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* 
                bblk = (size_t)in.B * in.N;
   const bool direct = bh_dev != nullptr;
   const bool gs = !direct && (in.stage2 == FBST_STAGE2_GS || in.stage2 == FBST_STAGE2_GS_IR1);
-  const bool beam_parts = !direct && in.stage2 == FBST_STAGE2_DENSE_TF32X3;
+  const bool beam_parts =
+      !direct && (in.stage2 == FBST_STAGE2_DENSE_TF32X3 || in.stage2 == FBST_STAGE2_DENSE_F16X3);
   // Everything earlier on s (including the previous chunk's reads of stage_y) precedes the copies in.
   FBST_CUDA_TRY(cudaEventRecord(ev[0], s));
   FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_in, ev[0], 0));
@@ -397,6 +399,7 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* 
     }
   }
   if (beam_parts) {
+    FBST_TRY(prepare_dense_tc_scales(p, p->ws_w, nb, s));  // one set of block scales for every beam range
     const int q2 = std::min(4, in.B);
     for (int r = 0; r < q2; ++r) {
       const int b0 = in.B * r / q2, b1 = in.B * (r + 1) / q2;

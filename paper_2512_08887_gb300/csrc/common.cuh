@@ -159,6 +159,8 @@ struct fbst_plan_s {
   float2* G;           // [B][N][L] complex64 (DENSE_FP32)
   void* Gtc;           // tensor-core operand (split-BF16 or TF32 layout), see dense_tc.cu
   size_t Gtc_bytes;
+  int* tc_gexp;        // [B] FP16 split: exponent of each beam's scale of G
+  float* tc_wpart;     // [max_blocks][16] FP16 split: partial maxima of |w| per block (its scale)
 
   double2* x64;        // [B][L] first column of A_b^{-1} (FP64), kept for inspection
 
@@ -263,6 +265,9 @@ int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* 
 // The TF32x3 operator of every beam applied to one right-hand side per block, w [nblk][L] (the
 // same for all beams); bhat [nblk][B][N].
 int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+// FP16-split tensor-core stage 2: the per-block scales of w (no-op for the other variants); stage 2
+// calls it itself, a caller that runs stage 2 by beam ranges calls it once before the ranges.
+int prepare_dense_tc_scales(const fbst_plan_s* p, const float2* w, int nblk, cudaStream_t s);
 int stage2_launches(const fbst_plan_s* p);
 // Stage 2 of the plan's variant on w [nb][B][L] -> bhat [nb][B][N] (nb <= max_blocks).
 int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s);

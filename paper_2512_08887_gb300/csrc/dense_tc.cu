@@ -31,6 +31,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <climits>
 #include <mutex>
@@ -40,7 +41,7 @@
 
 namespace fbst {
 
-enum tc_variant { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2 };
+enum tc_variant { TC_BF16X3 = 0, TC_TF32 = 1, TC_TF32X3 = 2, TC_F16X3 = 3 };
 
 template <int V> struct tc_traits;
 template <> struct tc_traits<TC_BF16X3> {
@@ -61,12 +62,14 @@ static int variant_of(int stage2) {
     case FBST_STAGE2_DENSE_BF16X3: return TC_BF16X3;
     case FBST_STAGE2_DENSE_TF32: return TC_TF32;
     case FBST_STAGE2_DENSE_TF32X3: return TC_TF32X3;
+    case FBST_STAGE2_DENSE_F16X3: return TC_F16X3;
     default: return -1;
   }
 }
 
 constexpr int kRowBytes = 128;    // one K-chunk row (the 128-byte swizzle span)
 constexpr int kTileM = 128;       // output samples per CTA (MMA M)
+constexpr int kWParts = 16;       // partial maxima per block of w (FP16 split: its scale)
 constexpr uint64_t kWaitNs = 1000000000ull;   // default limit of a pipeline wait (1 s; per plan)
 constexpr uint64_t kDrainNs = 2000000000ull;  // limit of the waits that drain copies / MMAs in flight
 
@@ -178,6 +181,8 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
@@ -438,13 +443,14 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 //                PERSIST)
 //   warps 2-3  : idle until the epilogue
 // ---------------------------------------------------------------------------------------------
-template <int NB>
+template <int NB, bool F16>
 struct fused_smem {
   static constexpr int RAW_STAGES = 2, PL_STAGES = 2;
   static constexpr int A_TILE = kTileM * kRowBytes;         // one FP32 plane of G: 128 rows x 32 K values
   static constexpr int W_BOX = NB * kRowBytes;              // raw w: NB rows x 16 complex values
   static constexpr int RAW_BYTES = 2 * A_TILE + 2 * W_BOX;  // TMA bytes of one stage (re, im, 2 w boxes)
-  static constexpr int WPL = 3 * NB * kRowBytes;            // one stacked plane [-W_im | W_re | W_im]
+  static constexpr int WROW = F16 ? 64 : kRowBytes;         // bytes of a 32-value K row of a w plane
+  static constexpr int WPL = 3 * NB * WROW;                 // one stacked plane [-W_im | W_re | W_im]
   static constexpr int PL_OFF = RAW_STAGES * RAW_BYTES;     // W planes: PL_STAGES x {hi, lo}
   static constexpr int BAR_OFF = PL_OFF + PL_STAGES * 2 * WPL;
   static constexpr int BAR_BYTES = 512;                     // mbarriers, tensor-memory slot, abort flag
@@ -468,6 +474,50 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
+// FP16 MMA (K = 16) with A in tensor memory (two FP16 values per 32-bit column, the lower K index
+// in the low half), B from a shared-memory descriptor.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// Shared-memory matrix descriptor, K-major operand in the 64-byte swizzle layout: rows of 64 bytes,
+// 8-row groups 512 bytes apart, 16-byte chunk c of row r stored at chunk c ^ ((r >> 1) & 3)
+// (address bits 4-5 XOR bits 7-8), version 1, swizzle mode 4.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// 2^e as a float, for |e| <= 126 (exact).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// The exponent e of the scale 2^e that maps a largest magnitude m into [2^14, 2^15) (frexp(m) =
+// f 2^x with f in [0.5, 1) gives e = 15 - x), so that every scaled value is below 2^15 and fits
+// FP16; 0 for m = 0 or a non-finite m.
+__host__ __device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f) || !(m <= 3.4e38f)) return 0;
+  int x;
+  (void)frexpf(m, &x);
+  const int e = 15 - x;
+  return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
+// The scale exponent of block blk from its kWParts partial maxima.
+__device__ __forceinline__ int block_scale_exp(const float* __restrict__ wpart, int blk) {
+  float m = 0.f;
+#pragma unroll
+  for (int i = 0; i < kWParts; ++i) m = fmaxf(m, wpart[blk * kWParts + i]);
+  return scale_exp(m);
+}
+
 // 16 consecutive 32-bit columns of this warp's 32 lanes (one value per thread and column).
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
   asm volatile(
@@ -478,15 +528,15 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
       : "memory");
 }
 
-template <int NB, bool PERSIST>
+template <int NB, bool PERSIST, bool F16>
 __global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int w_beam_mul,
-                 int* status, uint64_t wait_ns) {
-  using SM = fused_smem<NB>;
+                 const int* __restrict__ gexp, const float* __restrict__ wpart, int* status, uint64_t wait_ns) {
+  using SM = fused_smem<NB, F16>;
   constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
-  constexpr int KELEM = kRowBytes / 4;  // 32 FP32 values of K per chunk
-  constexpr int KSTEPS = KELEM / 8;     // MMAs of K = 8 per chunk and term
+  constexpr int KELEM = kRowBytes / 4;      // 32 FP32 values of K per chunk
+  constexpr int KSTEPS = KELEM / (F16 ? 16 : 8);  // MMAs of K = 8 (TF32) or 16 (FP16) per chunk and term
   constexpr uint32_t RING = 0, H0 = 32 * KSTEPS, H1 = H0 + 2 * NB, LO = H1 + 2 * NB;
   constexpr uint32_t COLS = LO + 2 * NB;
   constexpr uint32_t TMEM_COLS = COLS <= 256 ? 256 : 512;
@@ -557,14 +607,24 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
       int m0, b, blk0;
       tile_of(ti, m0, b, blk0);
-      if (!mbar_wait(tfull, it & 1, wait_ns)) {
+      // Both exits are taken by the whole warp (the loop below shuffles across its lanes).
+      const bool got = mbar_wait(tfull, it & 1, wait_ns);
+      if (!__all_sync(0xffffffffu, got)) {
         if (lane == 0) atomicExch(status, (int)FBST_ERR_TIMEOUT);
         *abort_flag = 1;
         break;
       }
-      if (*abort_flag) break;
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int n = m0 + ew * 32 + lane;
+      // FP16 split: undo the beam's scale of G and the blocks' scales of w (exact powers of two).
+      // Lane l holds the inverse scales of blocks blk0 + l and blk0 + 32 + l.
+      float ginv = 1.f, winv0 = 1.f, winv1 = 1.f;
+      if constexpr (F16) {
+        ginv = pow2f(-gexp[b]);
+        if (blk0 + lane < nblk) winv0 = pow2f(-block_scale_exp(wpart, blk0 + lane));
+        if (NB > 32 && blk0 + 32 + lane < nblk) winv1 = pow2f(-block_scale_exp(wpart, blk0 + 32 + lane));
+      }
 #pragma unroll 1
       for (int j0 = 0; j0 < NB; j0 += 16) {
         uint32_t h0r[16], h0i[16], lor[16], loi[16], h1r[16], h1i[16];
@@ -593,7 +653,13 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int blk = blk0 + j0 + jj;
-          if (blk < nblk && n < N) bhat[((size_t)blk * B + b) * N + n] = make_float2(re[jj] + t0[jj], im[jj] + t1[jj]);
+          float sc = 1.f;
+          if constexpr (F16) {
+            const int c = j0 + jj;  // the same for every lane: no divergence in the shuffle
+            sc = ginv * __shfl_sync(0xffffffffu, c < 32 ? winv0 : winv1, c & 31);
+          }
+          if (blk < nblk && n < N)
+            bhat[((size_t)blk * B + b) * N + n] = make_float2((re[jj] + t0[jj]) * sc, (im[jj] + t1[jj]) * sc);
         }
       }
     }
@@ -630,7 +696,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     for (int g = (issued > RS ? issued - RS : 0); g < issued; ++g) (void)mbar_wait(&full[g % RS], (g / RS) & 1, kDrainNs);
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t ID = make_idesc(2u, kTileM, 2 * NB, false);
+    constexpr uint32_t ID = make_idesc(F16 ? 0u : 2u, kTileM, 2 * NB, false);
     int gc = 0, it = 0;
     bool ok = true;
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
@@ -657,16 +723,28 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a = tmem + RING + 32 * k;  // [hi_re | hi_im | lo_re | lo_im], 8 columns each
-          // rows NB..3NB = [W_re | W_im] and rows 0..2NB = [-W_im | W_re] of the hi and lo planes
-          const uint64_t h1 = smem_desc_sw128(bh + NB * kRowBytes + k * 32), h2 = smem_desc_sw128(bh + k * 32);
-          const uint64_t l1 = smem_desc_sw128(bl + NB * kRowBytes + k * 32), l2 = smem_desc_sw128(bl + k * 32);
+          // rows NB..3NB = [W_re | W_im] and rows 0..2NB = [-W_im | W_re] of the hi and lo planes;
+          // a K step is 32 bytes of a row in both variants (8 TF32 or 16 FP16 values)
           const uint32_t hfirst = (c < 2 && k == 0) ? 0u : 1u, lfirst = (c == 0 && k == 0) ? 0u : 1u;
-          mma_tf32_ts(hacc, a + 0, h1, ID, hfirst);  // hi_re x [W_re | W_im]_hi
-          mma_tf32_ts(hacc, a + 8, h2, ID, 1u);      // hi_im x [-W_im | W_re]_hi
-          mma_tf32_ts(lacc, a + 0, l1, ID, lfirst);  // hi_re x lo
-          mma_tf32_ts(lacc, a + 8, l2, ID, 1u);      // hi_im x lo
-          mma_tf32_ts(lacc, a + 16, h1, ID, 1u);     // lo_re x hi
-          mma_tf32_ts(lacc, a + 24, h2, ID, 1u);     // lo_im x hi
+          if constexpr (F16) {
+            const uint64_t h1 = smem_desc_sw64(bh + NB * SM::WROW + k * 32), h2 = smem_desc_sw64(bh + k * 32);
+            const uint64_t l1 = smem_desc_sw64(bl + NB * SM::WROW + k * 32), l2 = smem_desc_sw64(bl + k * 32);
+            mma_f16_ts(hacc, a + 0, h1, ID, hfirst);
+            mma_f16_ts(hacc, a + 8, h2, ID, 1u);
+            mma_f16_ts(lacc, a + 0, l1, ID, lfirst);
+            mma_f16_ts(lacc, a + 8, l2, ID, 1u);
+            mma_f16_ts(lacc, a + 16, h1, ID, 1u);
+            mma_f16_ts(lacc, a + 24, h2, ID, 1u);
+          } else {
+            const uint64_t h1 = smem_desc_sw128(bh + NB * kRowBytes + k * 32), h2 = smem_desc_sw128(bh + k * 32);
+            const uint64_t l1 = smem_desc_sw128(bl + NB * kRowBytes + k * 32), l2 = smem_desc_sw128(bl + k * 32);
+            mma_tf32_ts(hacc, a + 0, h1, ID, hfirst);  // hi_re x [W_re | W_im]_hi
+            mma_tf32_ts(hacc, a + 8, h2, ID, 1u);      // hi_im x [-W_im | W_re]_hi
+            mma_tf32_ts(lacc, a + 0, l1, ID, lfirst);  // hi_re x lo
+            mma_tf32_ts(lacc, a + 8, l2, ID, 1u);      // hi_im x lo
+            mma_tf32_ts(lacc, a + 16, h1, ID, 1u);     // lo_re x hi
+            mma_tf32_ts(lacc, a + 24, h2, ID, 1u);     // lo_im x hi
+          }
           mma_commit(&afree[k]);
         }
         if (ok) mma_commit(&wfree[ps]);
@@ -689,6 +767,15 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     int gc = 0;
     bool ok = true;
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      // FP16 split: this tile's scale of G (its beam) and of the one w row (block) this thread
+      // converts, row ct % NB of the tile's blocks.
+      float gsc = 1.f, wsc = 1.f;
+      if constexpr (F16) {
+        int m0, b, blk0;
+        tile_of(ti, m0, b, blk0);
+        gsc = pow2f(gexp[b]);
+        if (blk0 + ct % NB < nblk) wsc = pow2f(block_scale_exp(wpart, blk0 + ct % NB));
+      }
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int s = gc % RS, ps = gc % PS;
         if (!mbar_wait(&full[s], (gc / RS) & 1, wait_ns) || *abort_flag) {
@@ -697,9 +784,9 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         }
         const uint8_t* raw = smem + s * SM::RAW_BYTES;
         // This thread's row of G for the whole chunk: 16-byte chunk j of row ct sits at j ^ (ct & 7).
-        float4 ar[2 * KSTEPS], ai[2 * KSTEPS];
+        float4 ar[KELEM / 4], ai[KELEM / 4];
 #pragma unroll
-        for (int j = 0; j < 2 * KSTEPS; ++j) {
+        for (int j = 0; j < KELEM / 4; ++j) {
           const int off = ct * kRowBytes + ((j ^ (ct & 7)) << 4);
           ar[j] = *reinterpret_cast<const float4*>(raw + off);
           ai[j] = *reinterpret_cast<const float4*>(raw + SM::A_TILE + off);
@@ -709,6 +796,46 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           break;
         }
         uint8_t* ph = smem + SM::PL_OFF + ps * 2 * SM::WPL;
+        if constexpr (F16) {
+          // B: 8 complex values (64 raw bytes) -> one 16-byte chunk (row r, chunk q of 4) of the -W_im,
+          // W_re and W_im rows of both FP16 planes, 64-byte swizzle. The raw boxes arrive in the
+          // 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7)) and consecutive threads take
+          // consecutive rows, so the 8 threads of a quarter warp read and write 8 different bank
+          // groups. Every item of this thread is in row ct % NB.
+#pragma unroll 2
+          for (int j = ct; j < NB * 4; j += 128) {
+            const int r = j % NB, q = j / NB;
+            const uint8_t* rp = raw + 2 * SM::A_TILE + (q >> 1) * SM::W_BOX + r * kRowBytes;
+            float4 x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              x[i] = *reinterpret_cast<const float4*>(rp + ((((q & 1) * 4 + i) ^ (r & 7)) << 4));
+            const float sc = wsc;
+            uint32_t rh[4], ih[4], nih[4], rl[4], il[4], nil[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float re0 = x[i].x * sc, im0 = x[i].y * sc, re1 = x[i].z * sc, im1 = x[i].w * sc;
+              const __half2 hr = __floats2half2_rn(re0, re1), hi2 = __floats2half2_rn(im0, im1);
+              const __half2 lr = __floats2half2_rn(re0 - __low2float(hr), re1 - __high2float(hr));
+              const __half2 li = __floats2half2_rn(im0 - __low2float(hi2), im1 - __high2float(hi2));
+              rh[i] = h2_bits(hr);
+              ih[i] = h2_bits(hi2);
+              nih[i] = ih[i] ^ 0x80008000u;
+              rl[i] = h2_bits(lr);
+              il[i] = h2_bits(li);
+              nil[i] = il[i] ^ 0x80008000u;
+            }
+            const int off = r * SM::WROW + ((q ^ ((r >> 1) & 3)) << 4);
+            uint8_t* hp = ph + off;
+            uint8_t* lp = ph + SM::WPL + off;
+            *reinterpret_cast<uint4*>(hp) = make_uint4(nih[0], nih[1], nih[2], nih[3]);
+            *reinterpret_cast<uint4*>(hp + NB * SM::WROW) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<uint4*>(hp + 2 * NB * SM::WROW) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+            *reinterpret_cast<uint4*>(lp) = make_uint4(nil[0], nil[1], nil[2], nil[3]);
+            *reinterpret_cast<uint4*>(lp + NB * SM::WROW) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<uint4*>(lp + 2 * NB * SM::WROW) = make_uint4(il[0], il[1], il[2], il[3]);
+          }
+        } else {
         // B: 4 complex values (32 raw bytes) -> one 16-byte chunk (row r, chunk q) of the -W_im, W_re
         // and W_im rows of both planes, at the swizzled position. The two raw halves are read in an
         // order that depends on the box, so the 8 threads of one row touch 8 different bank groups.
@@ -731,24 +858,43 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           *reinterpret_cast<float4*>(lp + NB * kRowBytes) = rl;
           *reinterpret_cast<float4*>(lp + 2 * NB * kRowBytes) = il;
         }
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&wconv[ps])) : "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&rawfree[s])) : "memory");
         // A: split each K step into tensor-memory slot k once the MMAs of the previous chunk freed it.
 #pragma unroll
         for (int k = 0; k < KSTEPS; ++k) {
-          const float x[2][8] = {{ar[2 * k].x, ar[2 * k].y, ar[2 * k].z, ar[2 * k].w, ar[2 * k + 1].x,
-                                  ar[2 * k + 1].y, ar[2 * k + 1].z, ar[2 * k + 1].w},
-                                 {ai[2 * k].x, ai[2 * k].y, ai[2 * k].z, ai[2 * k].w, ai[2 * k + 1].x,
-                                  ai[2 * k + 1].y, ai[2 * k + 1].z, ai[2 * k + 1].w}};
           uint32_t hi[16], lo[16];
+          if constexpr (F16) {
+            // K step k = 16 values per plane (float4s 4k..4k+3); column c holds values 2c, 2c+1.
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
+            for (int e = 0; e < 2; ++e) {
+              const float4* src = e ? ai : ar;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float h = round_tf32(x[e][i]);
-              hi[e * 8 + i] = __float_as_uint(h);
-              lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
+              for (int i = 0; i < 4; ++i) {
+                const float4 v = src[4 * k + i];
+                const float a0 = v.x * gsc, a1 = v.y * gsc, a2 = v.z * gsc, a3 = v.w * gsc;
+                const __half2 h01 = __floats2half2_rn(a0, a1), h23 = __floats2half2_rn(a2, a3);
+                hi[e * 8 + 2 * i] = h2_bits(h01);
+                hi[e * 8 + 2 * i + 1] = h2_bits(h23);
+                lo[e * 8 + 2 * i] = h2_bits(__floats2half2_rn(a0 - __low2float(h01), a1 - __high2float(h01)));
+                lo[e * 8 + 2 * i + 1] = h2_bits(__floats2half2_rn(a2 - __low2float(h23), a3 - __high2float(h23)));
+              }
+            }
+          } else {
+            const float x[2][8] = {{ar[2 * k].x, ar[2 * k].y, ar[2 * k].z, ar[2 * k].w, ar[2 * k + 1].x,
+                                    ar[2 * k + 1].y, ar[2 * k + 1].z, ar[2 * k + 1].w},
+                                   {ai[2 * k].x, ai[2 * k].y, ai[2 * k].z, ai[2 * k].w, ai[2 * k + 1].x,
+                                    ai[2 * k + 1].y, ai[2 * k + 1].z, ai[2 * k + 1].w}};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float h = round_tf32(x[e][i]);
+                hi[e * 8 + i] = __float_as_uint(h);
+                lo[e * 8 + i] = __float_as_uint(x[e][i] - h);
+              }
             }
           }
           if (gc >= 1 && !mbar_wait(&afree[k], (gc - 1) & 1, wait_ns)) {
@@ -796,6 +942,48 @@ __global__ void k_tc_planes_f32(const float2* __restrict__ G, float* __restrict_
   }
 }
 
+// Largest magnitude of any real or imaginary part of beam b's G planes ([2][N][L] FP32) ->
+// gexp[b], the exponent of the beam's FP16 scale (one CTA per beam).
+__global__ void k_tc_gexp(const float* __restrict__ planes, int* __restrict__ gexp, size_t per_beam) {
+  const float4* src = reinterpret_cast<const float4*>(planes + (size_t)blockIdx.x * per_beam);
+  float m = 0.f;
+  for (size_t i = threadIdx.x; i < per_beam / 4; i += blockDim.x) {
+    const float4 v = src[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) gexp[blockIdx.x] = scale_exp(m);
+  }
+}
+
+// Partial maxima of |re|, |im| over block blk of w (rows x 2L floats, contiguous per block):
+// part blockIdx.x of kWParts equal float4 ranges -> wpart[blk][part].
+__global__ void k_tc_wparts(const float* __restrict__ w, float* __restrict__ wpart, size_t per_block4) {
+  const int blk = blockIdx.y, part = blockIdx.x;
+  const float4* src = reinterpret_cast<const float4*>(w) + (size_t)blk * per_block4;
+  const size_t i0 = per_block4 * part / kWParts, i1 = per_block4 * (part + 1) / kWParts;
+  float m = 0.f;
+  for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const float4 v = src[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) wpart[blk * kWParts + part] = m;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
@@ -829,8 +1017,10 @@ static int make_map(CUtensorMap* map, const void* base, int esz, uint64_t X, uin
 }
 
 // 3-D map over the interleaved complex64 w [nblk][B][L] read as floats: dims {2L, B, nblk}, box
-// {32 floats, 1, boxZ}, no swizzle (the converter warps index it themselves).
-static int make_map_w(CUtensorMap* map, const void* base, uint64_t L2f, uint64_t B, uint64_t nblk, uint32_t boxZ) {
+// {32 floats, 1, boxZ}; no swizzle for the TF32 split (its converter warps index it themselves), the
+// 128-byte swizzle for the FP16 split.
+static int make_map_w(CUtensorMap* map, const void* base, uint64_t L2f, uint64_t B, uint64_t nblk, uint32_t boxZ,
+                      bool swizzle128 = false) {
   auto enc = tensor_map_encoder();
   if (!enc) return FBST_ERR_UNSUPPORTED;
   const cuuint64_t dims[3] = {L2f, B, nblk};
@@ -838,8 +1028,9 @@ static int make_map_w(CUtensorMap* map, const void* base, uint64_t L2f, uint64_t
   const cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / 4), 1, boxZ};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? FBST_OK : FBST_ERR_CUDA;
 }
 
@@ -866,7 +1057,7 @@ static int build_operand_V(fbst_plan_s* p, cudaStream_t s) {
   return FBST_OK;
 }
 
-static int build_operand_fused(fbst_plan_s* p, cudaStream_t s) {
+static int build_operand_fused(fbst_plan_s* p, bool f16, cudaStream_t s) {
   const fbst_info& in = p->info;
   if (in.L % 8 != 0) return FBST_ERR_UNSUPPORTED;
   const size_t bytes = (size_t)in.B * 2 * in.N * in.L * sizeof(float);
@@ -874,6 +1065,13 @@ static int build_operand_fused(fbst_plan_s* p, cudaStream_t s) {
   p->Gtc_bytes = bytes;
   k_tc_planes_f32<<<4096, 256, 0, s>>>(p->G, static_cast<float*>(p->Gtc), in.B, in.N, in.L);
   FBST_CUDA_TRY(cudaGetLastError());
+  if (f16) {
+    // The FP16 split scales each beam's G and each block's w by a power of two.
+    FBST_TRY(plan_alloc_n(p, &p->tc_gexp, (size_t)in.B));
+    FBST_TRY(plan_alloc_n(p, &p->tc_wpart, (size_t)p->band.max_blocks * kWParts));
+    k_tc_gexp<<<in.B, 256, 0, s>>>(static_cast<const float*>(p->Gtc), p->tc_gexp, (size_t)2 * in.N * in.L);
+    FBST_CUDA_TRY(cudaGetLastError());
+  }
   return FBST_OK;
 }
 
@@ -882,7 +1080,8 @@ int build_dense_tc_operand(fbst_plan_s* p, cudaStream_t s) {
   switch (variant_of(p->info.stage2)) {
     case TC_BF16X3: return build_operand_V<TC_BF16X3>(p, s);
     case TC_TF32: return build_operand_V<TC_TF32>(p, s);
-    case TC_TF32X3: return build_operand_fused(p, s);
+    case TC_TF32X3: return build_operand_fused(p, false, s);
+    case TC_F16X3: return build_operand_fused(p, true, s);
     default: return FBST_ERR_INVALID;
   }
 }
@@ -925,7 +1124,7 @@ static int launch_V(const fbst_plan_s* p, const float2* w, float2* bhat, int nbl
   return FBST_ERR_INVALID;
 }
 
-template <int NB>
+template <int NB, bool F16>
 static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                       bool shared_rhs, cudaStream_t s) {
   const fbst_info& in = p->info;
@@ -933,32 +1132,52 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   int r = make_map(&mapA, p->Gtc, 4, in.L, in.N, (uint64_t)in.B * 2, kTileM);
   if (r != FBST_OK) return r;
   // A shared right-hand side is one row per block that every beam reads (beam coordinate 0).
-  r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, shared_rhs ? 1 : in.B, nblk, NB);
+  r = make_map_w(&mapW, w, 2 * (uint64_t)in.L, shared_rhs ? 1 : in.B, nblk, NB, F16);
   if (r != FBST_OK) return r;
   // NB >= 32: one CTA per SM is all that shared and tensor memory allow, so it is persistent and
   // walks its tiles. NB = 16: two single-tile CTAs (256 threads, 256 tensor-memory columns) fit
   // on an SM, which keeps more of G in flight than one persistent CTA does.
   constexpr bool kPersist = NB >= 32;
-  const int smem = fused_smem<NB>::BYTES;
-  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB, kPersist>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem));
+  const int smem = fused_smem<NB, F16>::BYTES;
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_dense_tc_fused<NB, kPersist, F16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long ntiles = (long long)((in.N + kTileM - 1) / kTileM) * nbeam * ((nblk + NB - 1) / NB);
   if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
   const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
-  k_dense_tc_fused<NB, kPersist><<<grid, kPersist ? 384 : 256, smem, s>>>(mapA, mapW, bhat, in.B, in.N, in.L, nblk,
-                                                                           b0, nbeam, shared_rhs ? 0 : 1,
-                                                                           p->d_status,
-      p->wait_ns ? p->wait_ns : kWaitNs);
+  k_dense_tc_fused<NB, kPersist, F16><<<grid, kPersist ? 384 : 256, smem, s>>>(
+      mapA, mapW, bhat, in.B, in.N, in.L, nblk, b0, nbeam, shared_rhs ? 0 : 1, p->tc_gexp, p->tc_wpart,
+      p->d_status, p->wait_ns ? p->wait_ns : kWaitNs);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
+template <bool F16>
+static int launch_fused_F(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
+                          cudaStream_t s, bool shared_rhs) {
+  const int want = std::min(round16(nblk), 64);
+  if (want <= 16) return gemm_fused<16, F16>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+  if (want <= 32) return gemm_fused<32, F16>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+  return gemm_fused<64, F16>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+}
+
 static int launch_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                         cudaStream_t s, bool shared_rhs = false) {
-  const int want = std::min(round16(nblk), 64);
-  if (want <= 16) return gemm_fused<16>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
-  if (want <= 32) return gemm_fused<32>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
-  return gemm_fused<64>(p, w, bhat, nblk, b0, nbeam, shared_rhs, s);
+  if (variant_of(p->info.stage2) == TC_F16X3) return launch_fused_F<true>(p, w, bhat, nblk, b0, nbeam, s, shared_rhs);
+  return launch_fused_F<false>(p, w, bhat, nblk, b0, nbeam, s, shared_rhs);
+}
+
+static bool fused_variant(const fbst_plan_s* p) {
+  const int v = variant_of(p->info.stage2);
+  return v == TC_TF32X3 || v == TC_F16X3;
+}
+
+int prepare_dense_tc_scales(const fbst_plan_s* p, const float2* w, int nblk, cudaStream_t s) {
+  if (variant_of(p->info.stage2) != TC_F16X3 || nblk <= 0) return FBST_OK;
+  if (!p->tc_wpart || nblk > p->band.max_blocks || nblk > 65535) return FBST_ERR_INVALID;
+  const size_t per_block4 = (size_t)p->info.B * p->info.L / 2;  // B x L complex64 = B L / 2 float4
+  k_tc_wparts<<<dim3(kWParts, nblk), 256, 0, s>>>(reinterpret_cast<const float*>(w), p->tc_wpart, per_block4);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
 }
 
 int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
@@ -970,7 +1189,7 @@ int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bh
 
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                                  cudaStream_t s) {
-  if (variant_of(p->info.stage2) != TC_TF32X3) return FBST_ERR_UNSUPPORTED;
+  if (!fused_variant(p)) return FBST_ERR_UNSUPPORTED;
   if (b0 < 0 || nbeam < 0 || b0 + nbeam > p->info.B) return FBST_ERR_INVALID;
   if (nblk <= 0 || nbeam == 0) return FBST_OK;
   if (!p->Gtc) return FBST_ERR_INVALID;
@@ -980,7 +1199,10 @@ int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* 
 int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
   if (!p->Gtc) return FBST_ERR_INVALID;
-  if (variant_of(p->info.stage2) == TC_TF32X3) return launch_fused(p, w, bhat, nblk, 0, p->info.B, s);
+  if (fused_variant(p)) {
+    FBST_TRY(prepare_dense_tc_scales(p, w, nblk, s));
+    return launch_fused(p, w, bhat, nblk, 0, p->info.B, s);
+  }
   if (!p->ws_tc) return FBST_ERR_INVALID;
   switch (variant_of(p->info.stage2)) {
     case TC_BF16X3: return launch_V<TC_BF16X3>(p, w, bhat, nblk, s);

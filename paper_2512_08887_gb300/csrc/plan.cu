@@ -90,7 +90,8 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
   if (band->max_blocks < 1) return FBST_ERR_INVALID;
   switch (band->stage2) {
     case FBST_STAGE2_AUTO: case FBST_STAGE2_GS: case FBST_STAGE2_GS_IR1: case FBST_STAGE2_DENSE_FP32:
-    case FBST_STAGE2_DENSE_BF16X3: case FBST_STAGE2_DENSE_TF32: case FBST_STAGE2_DENSE_TF32X3: break;
+    case FBST_STAGE2_DENSE_BF16X3: case FBST_STAGE2_DENSE_TF32: case FBST_STAGE2_DENSE_TF32X3:
+    case FBST_STAGE2_DENSE_F16X3: break;
     default: return FBST_ERR_INVALID;
   }
   const int L = (int)L64;
@@ -168,12 +169,15 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
     // G_b in complex64 (FP32 apply), or its tensor-core planes (8 bytes per entry in every
     // variant; the complex64 G_b is freed once they are built).
     tb += c64 * (size_t)B * N * L;
+    if (out->stage2 == FBST_STAGE2_DENSE_F16X3) tb += sizeof(int) * (size_t)B;  // beam scales of G
   }
   out->table_bytes = tb;
   out->workspace_bytes = c64 * (size_t)band->max_blocks * ((size_t)L * M + (size_t)B * L);
   // The pre-split right-hand sides of the BF16x3 and TF32 tensor-core variants.
   if (out->stage2 == FBST_STAGE2_DENSE_BF16X3 || out->stage2 == FBST_STAGE2_DENSE_TF32)
     out->workspace_bytes += c64 * (size_t)B * (((size_t)band->max_blocks + 15) / 16 * 16) * L;
+  // The partial maxima of w behind the block scales of the FP16-split variant.
+  if (out->stage2 == FBST_STAGE2_DENSE_F16X3) out->workspace_bytes += sizeof(float) * 16 * (size_t)band->max_blocks;
   return FBST_OK;
 }
 

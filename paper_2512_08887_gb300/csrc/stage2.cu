@@ -274,6 +274,7 @@ int stage2_launches(const fbst_plan_s* p) {
     case FBST_STAGE2_GS_IR1: return 1;
     case FBST_STAGE2_DENSE_FP32: return 1;
     case FBST_STAGE2_DENSE_TF32X3: return 1;  // fused: splits its operands in shared memory
+    case FBST_STAGE2_DENSE_F16X3: return 2;   // the block scales of w, then the fused GEMM
     default: return 2;  // other tensor-core variants: operand preparation + GEMM
   }
 }

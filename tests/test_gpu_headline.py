@@ -64,7 +64,7 @@ def ula1024():
     return d, pb, ref
 
 
-@pytest.mark.parametrize("stage2", ["dense_tf32x3", "gs_ir1"])
+@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_f16x3", "gs_ir1"])
 def test_execute_ula1024_all_blocks(ula1024, stage2):
     d, pb0, ref = ula1024
     plan, pb = _plan(stage2, 1024, 512, 0.5, 64)

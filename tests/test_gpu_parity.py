@@ -181,7 +181,7 @@ def test_chunking_host_path_and_determinism(rng):
     assert O.rel_l2(a, O.fbst(pb, y)) < TOL_E2E
 
 
-@pytest.mark.parametrize("stage2", ["gs_ir1", "dense_tf32x3", "dense_fp32"])
+@pytest.mark.parametrize("stage2", ["gs_ir1", "dense_tf32x3", "dense_f16x3", "dense_fp32"])
 def test_pipelined_host_path_equals_device_path(rng, stage2):
     # fbst_execute_host overlaps its copies with the kernels: stage 1 and the copies in run in block
     # parts; stage 2 and the copies out run in block parts (Gohberg-Semencul), in beam ranges with
@@ -198,7 +198,7 @@ def test_pipelined_host_path_equals_device_path(rng, stage2):
     assert O.rel_l2(host_out, O.fbst(pb, y)) < TOL_E2E
 
 
-@pytest.mark.parametrize("stage2", ["gs_ir1", "dense_tf32x3"])
+@pytest.mark.parametrize("stage2", ["gs_ir1", "dense_tf32x3", "dense_f16x3"])
 def test_host_path_with_pinned_output_writes_in_place(rng, stage2):
     # A pinned output buffer is written by stage 2 through its device address (no copy out).
     y = crandn(rng, 7, 40, 96)
@@ -237,10 +237,10 @@ def test_on_grid_plane_wave_is_reproduced_on_gpu():
     assert O.rel_l2(got[0, b], waveform(src, np.arange(64))) < 1e-2
 
 
-TC_TOL = {"dense_tf32x3": TOL_E2E, "dense_bf16x3": 1e-3, "dense_tf32": 3e-2}
+TC_TOL = {"dense_tf32x3": TOL_E2E, "dense_f16x3": TOL_E2E, "dense_bf16x3": 1e-3, "dense_tf32": 3e-2}
 
 
-@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_bf16x3", "dense_tf32"])
+@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_f16x3", "dense_bf16x3", "dense_tf32"])
 @pytest.mark.parametrize("case", [("ula", 16, 1, 16, 1, 64, 0.5, 3), ("ula", 13, 1, 10, 1, 24, 0.37, 5),
                                   ("ura", 8, 8, 8, 8, 64, 0.3, 2), ("ula", 48, 1, 40, 1, 256, 0.5, 70),
                                   ("ula", 40, 1, 160, 1, 200, 0.45, 27)])
@@ -269,7 +269,7 @@ def test_execute_c3_precision_split_sampled_beams():
     d = configs.config_data("C3", nblk=4, Q=64)
     beams = np.array([0, 33, 500, 777, 1023])
     errs, ref = {}, None
-    for stage2 in ("dense_tf32x3", "dense_bf16x3", "dense_tf32"):
+    for stage2 in ("dense_tf32x3", "dense_f16x3", "dense_bf16x3", "dense_tf32"):
         plan, pb = make("ura", 32, 32, 32, 32, 512, 0.3, stage2=stage2, max_blocks=4)
         got = run(plan, "execute", d["y"], (4, 1024, 512), 4)
         assert plan.sync_status() == 0
@@ -278,7 +278,8 @@ def test_execute_c3_precision_split_sampled_beams():
         errs[stage2] = O.rel_l2(got[:, beams], ref)
         plan.close()
     print("C3 rel L2 error vs FP64 oracle:", {k: f"{v:.2e}" for k, v in errs.items()})
-    assert errs["dense_tf32x3"] < TOL_E2E and errs["dense_bf16x3"] < 1e-3 and errs["dense_tf32"] < 3e-2, errs
+    assert errs["dense_tf32x3"] < TOL_E2E and errs["dense_f16x3"] < TOL_E2E, errs
+    assert errs["dense_bf16x3"] < 1e-3 and errs["dense_tf32"] < 3e-2, errs
 
 
 def test_execute_c2_full_size_tf32x3_sampled_beams():
@@ -295,7 +296,7 @@ def test_execute_c2_full_size_tf32x3_sampled_beams():
     assert np.isfinite(got).all()
 
 
-@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_bf16x3"])
+@pytest.mark.parametrize("stage2", ["dense_tf32x3", "dense_f16x3", "dense_bf16x3"])
 def test_tensor_core_wait_that_runs_out_reports_timeout_and_recovers(rng, stage2):
     # Failure detection without a fault: a wait limit of 1 ns makes the pipeline waits of the
     # tensor-core kernel run out (nothing can complete that fast). The kernel must record
@@ -316,3 +317,23 @@ def test_tensor_core_wait_that_runs_out_reports_timeout_and_recovers(rng, stage2
     assert plan.sync_status() == 0
     got = out2.cpu().numpy()[:2]
     assert O.rel_l2(got, O.Stage2Factors(pb).apply(w)) < TC_TOL[stage2]
+
+
+def test_f16x3_block_scales_keep_accuracy_across_magnitudes(rng):
+    # The FP16 split scales G per beam and w per block by powers of two chosen from their largest
+    # magnitudes, so every block keeps FP32-class accuracy however large or small it is, in one
+    # call with blocks 50 orders of magnitude apart and an all-zero block (scale 1, output 0).
+    plan, pb = make("ula", 48, 1, 40, 1, 256, 0.5, stage2="dense_f16x3", max_blocks=6)
+    y = crandn(rng, 6, 48, 256)
+    w = O.fan_coefficients(pb, y).astype(np.complex64)
+    mags = np.array([1e-25, 1e-3, 1.0, 1e3, 1e25, 0.0], dtype=np.float32)
+    ws = (w * mags[:, None, None]).astype(np.complex64)
+    got = run(plan, "toeplitz_apply", ws, (6, pb.B, 256), 6)
+    assert plan.sync_status() == 0
+    ref = O.Stage2Factors(pb).apply(w)
+    for i, m in enumerate(mags):
+        if m == 0:
+            assert not got[i].any()
+        else:
+            err = O.rel_l2(got[i] / np.float64(m), ref[i])
+            assert err < TOL_E2E, f"block scaled by {m:g}: {err:.3e}"
