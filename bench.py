@@ -4,9 +4,10 @@ Default workload (ULA1024): 1024-element linear array, fb = 0.5, N = 512 snapsho
 B = 1024 beams, L = 1024, 64 contiguous blocks of one record per step, complex64 in and out. This
 is the array size (M = B = 1024) at which the transform's roofline is stated. Stage 1 (the fan
 chirp-z) runs in FP32 on the CUDA cores; stage 2 by default is the precomputed-inverse apply on the
-tensor cores in split TF32 with split FP32 accumulation (FP32-class: its error against the FP64
-oracle is measured and reported on every run); --stage2 gs_ir1 selects the Gohberg-Semencul path,
-dense_fp32 the CUDA-core apply. One step = fbst_execute over the 64 blocks.
+tensor cores in split FP16 (hi + lo halves with exact power-of-two scales) with split FP32
+accumulation (FP32-class: its error against the FP64 oracle is measured and reported on every run);
+--stage2 dense_tf32x3 selects the split-TF32 form, gs_ir1 the Gohberg-Semencul path, dense_fp32 the
+CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
                   [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|OG|STREAM] [--contraction tf32x3|fp32]
@@ -76,7 +77,8 @@ def flop_model(info) -> dict:
 
 # Tensor-core variants: (planes of G, bytes per element, products per complex term, peak dtype,
 # passes over w: prepared planes = read + write + read; the fused TF32x3 kernel reads w once; the
-# fused FP16x3 kernel reads it once more for the block scales). FP16 MMAs run at the BF16 rate.
+# FP16x3 stage-2 call reads it once more for the block scales, which the whole transform takes from
+# stage 1b instead). FP16 MMAs run at the BF16 rate.
 TC_VARIANTS = {4: (4, 2, 3, "bf16", 3), 5: (2, 4, 1, "tf32", 3), 6: (2, 4, 3, "tf32", 1), 7: (2, 4, 3, "f16", 2)}
 
 
@@ -920,7 +922,7 @@ def main() -> None:
     ap.add_argument("--impl", default="fbst", choices=["fbst", "reference"])
     ap.add_argument("--workload", default="ULA1024")
     ap.add_argument("--nblk", type=int, default=None)
-    ap.add_argument("--stage2", default="dense_tf32x3")
+    ap.add_argument("--stage2", default="dense_f16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--contraction", default="fp32", choices=["tf32x3", "fp32"])

@@ -81,7 +81,7 @@ static int dmalloc(fbst_plan_s* p, T** ptr, size_t count) {
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
-int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s) {
+int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s, bool w_from_stage1) {
   switch (p->info.stage2) {
     case FBST_STAGE2_GS:
     case FBST_STAGE2_GS_IR1: return launch_stage2_gs(p, w, bhat, nb, s);
@@ -89,7 +89,7 @@ int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cuda
     case FBST_STAGE2_DENSE_BF16X3:
     case FBST_STAGE2_DENSE_TF32:
     case FBST_STAGE2_DENSE_TF32X3:
-    case FBST_STAGE2_DENSE_F16X3: return launch_stage2_dense_tc(p, w, bhat, nb, s);
+    case FBST_STAGE2_DENSE_F16X3: return launch_stage2_dense_tc(p, w, bhat, nb, s, w_from_stage1 && p->tc_wmax_stage1);
     default: return FBST_ERR_INVALID;
   }
 }
@@ -347,8 +347,8 @@ int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* strea
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
     FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
-    FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nb, s));
-    FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s));
+    FBST_TRY(launch_czt_space_scaled(p, p->ws_yhat, p->ws_w, nb, 0, s));
+    FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s, true));
   }
   return FBST_OK;
 }
@@ -389,7 +389,7 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* 
     FBST_CUDA_TRY(cudaEventRecord(ev[1 + i], ci));
     FBST_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + i], 0));
     FBST_TRY(launch_czt_time(p, p->stage_y + a * yblk, p->ws_yhat + a * hblk, (int)(e - a), s));
-    FBST_TRY(launch_czt_space(p, p->ws_yhat + a * hblk, p->ws_w + a * wblk, (int)(e - a), s));
+    FBST_TRY(launch_czt_space_scaled(p, p->ws_yhat + a * hblk, p->ws_w + a * wblk, (int)(e - a), (int)a, s));
     if (gs) {
       FBST_TRY(run_stage2(p, p->ws_w + a * wblk, p->stage_bhat + a * bblk, (int)(e - a), s));
       FBST_CUDA_TRY(cudaEventRecord(ev[5 + i], s));
@@ -399,7 +399,8 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* 
     }
   }
   if (beam_parts) {
-    FBST_TRY(prepare_dense_tc_scales(p, p->ws_w, nb, s));  // one set of block scales for every beam range
+    // One set of block scales for every beam range (already written by stage 1b on a grid array).
+    if (!p->tc_wmax_stage1) FBST_TRY(prepare_dense_tc_scales(p, p->ws_w, nb, s));
     const int q2 = std::min(4, in.B);
     for (int r = 0; r < q2; ++r) {
       const int b0 = in.B * r / q2, b1 = in.B * (r + 1) / q2;
@@ -413,10 +414,10 @@ static int execute_host_chunk(fbst_plan_s* p, const char* yh, char* bh, float2* 
                                       p->copy_out));
     }
   } else if (direct) {
-    FBST_TRY(run_stage2(p, p->ws_w, bh_dev, nb, s));
+    FBST_TRY(run_stage2(p, p->ws_w, bh_dev, nb, s, true));
     return FBST_OK;
   } else if (!gs) {
-    FBST_TRY(run_stage2(p, p->ws_w, p->stage_bhat, nb, s));
+    FBST_TRY(run_stage2(p, p->ws_w, p->stage_bhat, nb, s, true));
     FBST_CUDA_TRY(cudaEventRecord(ev[5], s));
     FBST_CUDA_TRY(cudaStreamWaitEvent(p->copy_out, ev[5], 0));
     FBST_CUDA_TRY(cudaMemcpyAsync(bh, p->stage_bhat, sizeof(float2) * (size_t)nb * bblk, cudaMemcpyDeviceToHost,
@@ -470,7 +471,7 @@ int fbst_execute_host(fbst_plan_t p, const void* y_host, void* bhat_host, int nb
 int fbst_launch_count(fbst_plan_t p, int nblk) {
   if (!p || nblk <= 0) return 0;
   const int chunks = (nblk + p->band.max_blocks - 1) / p->band.max_blocks;
-  return chunks * (2 + stage2_launches(p));
+  return chunks * (2 + stage2_launches(p, true));
 }
 
 }  // extern "C"

@@ -66,6 +66,7 @@ struct space_job {     // spatial chirp-z (linear array) of one plan over nblk b
   const float2* post;
   int M, B, L, nblk;
   long long first;
+  unsigned* wmax;      // null, or [nblk]: atomic max of |re|, |im| of each block's w (float bits)
 };
 
 struct gs_job {        // Gohberg-Semencul stage 2 + reconstruction of one plan over nblk blocks
@@ -160,7 +161,8 @@ struct fbst_plan_s {
   void* Gtc;           // tensor-core operand (split-BF16 or TF32 layout), see dense_tc.cu
   size_t Gtc_bytes;
   int* tc_gexp;        // [B] FP16 split: exponent of each beam's scale of G
-  float* tc_wpart;     // [max_blocks][16] FP16 split: partial maxima of |w| per block (its scale)
+  unsigned* tc_wmax;   // [max_blocks] FP16 split: largest |re|, |im| of each block of w (float bits)
+  bool tc_wmax_stage1; // FP16 split on a linear grid array: the spatial chirp-z writes tc_wmax
 
   double2* x64;        // [B][L] first column of A_b^{-1} (FP64), kept for inspection
 
@@ -231,6 +233,10 @@ int launch_czt_time(const fbst_plan_s* p, const float2* y, float2* yhat, int nbl
 int launch_czt_time_record(const fbst_plan_s* p, const float2* record, long long T, int hop, float2* yhat, int nblk,
                            cudaStream_t s);
 int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s);
+// The same, and when p->tc_wmax_stage1 also the block maxima of w into p->tc_wmax + blk0 (blocks
+// blk0 .. blk0 + nblk - 1 of the chunk that stage 2 will take).
+int launch_czt_space_scaled(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, int blk0,
+                            cudaStream_t s);
 int launch_stage2_gs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
 
 // Multi-job launchers: every job of `jl` shares the transform size P (and for stage 2 the
@@ -258,19 +264,24 @@ int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat
 // shared_rhs is set.
 int launch_dense_fp32_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, bool shared_rhs,
                           cudaStream_t s);
-int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
+// scales_ready: tc_wmax already holds the block maxima of this w (written by the spatial chirp-z).
+int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s,
+                           bool scales_ready = false);
 // The TF32x3 operator for beams [b0, b0 + nbeam) only (FBST_ERR_UNSUPPORTED for other variants).
 int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, int b0, int nbeam,
                                  cudaStream_t s);
 // The TF32x3 operator of every beam applied to one right-hand side per block, w [nblk][L] (the
 // same for all beams); bhat [nblk][B][N].
 int launch_dense_tc_shared_rhs(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s);
-// FP16-split tensor-core stage 2: the per-block scales of w (no-op for the other variants); stage 2
-// calls it itself, a caller that runs stage 2 by beam ranges calls it once before the ranges.
+// FP16-split tensor-core stage 2: the block maxima of w in tc_wmax, from w itself (no-op for the
+// other variants); stage 2 calls it unless the spatial chirp-z has written them, a caller that runs
+// stage 2 by beam ranges calls it once before the ranges.
 int prepare_dense_tc_scales(const fbst_plan_s* p, const float2* w, int nblk, cudaStream_t s);
-int stage2_launches(const fbst_plan_s* p);
+int stage2_launches(const fbst_plan_s* p, bool w_from_stage1);
 // Stage 2 of the plan's variant on w [nb][B][L] -> bhat [nb][B][N] (nb <= max_blocks).
-int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s);
+// w_from_stage1: w was written by launch_czt_space_scaled with the plan's tc_wmax in this call.
+int run_stage2(const fbst_plan_s* p, const float2* w, float2* bhat, int nb, cudaStream_t s,
+               bool w_from_stage1 = false);
 
 // Plan-time builders (plan.cu / dense_tc.cu).
 int build_plan_tables(fbst_plan_s* p, cudaStream_t s);

@@ -69,7 +69,7 @@ static int variant_of(int stage2) {
 
 constexpr int kRowBytes = 128;    // one K-chunk row (the 128-byte swizzle span)
 constexpr int kTileM = 128;       // output samples per CTA (MMA M)
-constexpr int kWParts = 16;       // partial maxima per block of w (FP16 split: its scale)
+constexpr int kWParts = 16;       // CTAs per block of w that find its largest magnitude (FP16 split)
 constexpr uint64_t kWaitNs = 1000000000ull;   // default limit of a pipeline wait (1 s; per plan)
 constexpr uint64_t kDrainNs = 2000000000ull;  // limit of the waits that drain copies / MMAs in flight
 
@@ -445,7 +445,8 @@ k_dense_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------------------------
 template <int NB, bool F16>
 struct fused_smem {
-  static constexpr int RAW_STAGES = 2, PL_STAGES = 2;
+  // The FP16 planes are half the size, so a persistent CTA (NB >= 32) fits one more raw stage.
+  static constexpr int RAW_STAGES = (F16 && NB >= 32) ? 3 : 2, PL_STAGES = 2;
   static constexpr int A_TILE = kTileM * kRowBytes;         // one FP32 plane of G: 128 rows x 32 K values
   static constexpr int W_BOX = NB * kRowBytes;              // raw w: NB rows x 16 complex values
   static constexpr int RAW_BYTES = 2 * A_TILE + 2 * W_BOX;  // TMA bytes of one stage (re, im, 2 w boxes)
@@ -510,12 +511,9 @@ __host__ __device__ __forceinline__ int scale_exp(float m) {
   return e < -120 ? -120 : (e > 120 ? 120 : e);
 }
 
-// The scale exponent of block blk from its kWParts partial maxima.
-__device__ __forceinline__ int block_scale_exp(const float* __restrict__ wpart, int blk) {
-  float m = 0.f;
-#pragma unroll
-  for (int i = 0; i < kWParts; ++i) m = fmaxf(m, wpart[blk * kWParts + i]);
-  return scale_exp(m);
+// The scale exponent of block blk from its largest |re|, |im| (float bits).
+__device__ __forceinline__ int block_scale_exp(const unsigned* __restrict__ wmax, int blk) {
+  return scale_exp(__uint_as_float(wmax[blk]));
 }
 
 // 16 consecutive 32-bit columns of this warp's 32 lanes (one value per thread and column).
@@ -532,7 +530,7 @@ template <int NB, bool PERSIST, bool F16>
 __global__ void __launch_bounds__(PERSIST ? 384 : 256, PERSIST ? 1 : 2)
 k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapW,
                  float2* __restrict__ bhat, int B, int N, int L, int nblk, int b0, int nbeam, int w_beam_mul,
-                 const int* __restrict__ gexp, const float* __restrict__ wpart, int* status, uint64_t wait_ns) {
+                 const int* __restrict__ gexp, const unsigned* __restrict__ wmax, int* status, uint64_t wait_ns) {
   using SM = fused_smem<NB, F16>;
   constexpr int RS = SM::RAW_STAGES, PS = SM::PL_STAGES;
   constexpr int KELEM = kRowBytes / 4;      // 32 FP32 values of K per chunk
@@ -622,8 +620,8 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       float ginv = 1.f, winv0 = 1.f, winv1 = 1.f;
       if constexpr (F16) {
         ginv = pow2f(-gexp[b]);
-        if (blk0 + lane < nblk) winv0 = pow2f(-block_scale_exp(wpart, blk0 + lane));
-        if (NB > 32 && blk0 + 32 + lane < nblk) winv1 = pow2f(-block_scale_exp(wpart, blk0 + 32 + lane));
+        if (blk0 + lane < nblk) winv0 = pow2f(-block_scale_exp(wmax, blk0 + lane));
+        if (NB > 32 && blk0 + 32 + lane < nblk) winv1 = pow2f(-block_scale_exp(wmax, blk0 + 32 + lane));
       }
 #pragma unroll 1
       for (int j0 = 0; j0 < NB; j0 += 16) {
@@ -774,7 +772,7 @@ k_dense_tc_fused(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         int m0, b, blk0;
         tile_of(ti, m0, b, blk0);
         gsc = pow2f(gexp[b]);
-        if (blk0 + ct % NB < nblk) wsc = pow2f(block_scale_exp(wpart, blk0 + ct % NB));
+        if (blk0 + ct % NB < nblk) wsc = pow2f(block_scale_exp(wmax, blk0 + ct % NB));
       }
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int s = gc % RS, ps = gc % PS;
@@ -962,9 +960,10 @@ __global__ void k_tc_gexp(const float* __restrict__ planes, int* __restrict__ ge
   }
 }
 
-// Partial maxima of |re|, |im| over block blk of w (rows x 2L floats, contiguous per block):
-// part blockIdx.x of kWParts equal float4 ranges -> wpart[blk][part].
-__global__ void k_tc_wparts(const float* __restrict__ w, float* __restrict__ wpart, size_t per_block4) {
+// Largest |re|, |im| over block blk of w (rows x 2L floats, contiguous per block): kWParts CTAs per
+// block, each over an equal float4 range, combine by atomicMax on the float bits into wmax[blk]
+// (zeroed first; the maximum does not depend on the order).
+__global__ void k_tc_wmax(const float* __restrict__ w, unsigned* __restrict__ wmax, size_t per_block4) {
   const int blk = blockIdx.y, part = blockIdx.x;
   const float4* src = reinterpret_cast<const float4*>(w) + (size_t)blk * per_block4;
   const size_t i0 = per_block4 * part / kWParts, i1 = per_block4 * (part + 1) / kWParts;
@@ -980,7 +979,7 @@ __global__ void k_tc_wparts(const float* __restrict__ w, float* __restrict__ wpa
   if (threadIdx.x < 32) {
     m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) wpart[blk * kWParts + part] = m;
+    if (threadIdx.x == 0) atomicMax(wmax + blk, __float_as_uint(m));
   }
 }
 
@@ -1068,7 +1067,9 @@ static int build_operand_fused(fbst_plan_s* p, bool f16, cudaStream_t s) {
   if (f16) {
     // The FP16 split scales each beam's G and each block's w by a power of two.
     FBST_TRY(plan_alloc_n(p, &p->tc_gexp, (size_t)in.B));
-    FBST_TRY(plan_alloc_n(p, &p->tc_wpart, (size_t)p->band.max_blocks * kWParts));
+    FBST_TRY(plan_alloc_n(p, &p->tc_wmax, (size_t)p->band.max_blocks));
+    // The spatial chirp-z of a linear grid array finds the block maxima as it writes w.
+    p->tc_wmax_stage1 = p->geom.kind == FBST_ULA && !p->nu_nf;
     k_tc_gexp<<<in.B, 256, 0, s>>>(static_cast<const float*>(p->Gtc), p->tc_gexp, (size_t)2 * in.N * in.L);
     FBST_CUDA_TRY(cudaGetLastError());
   }
@@ -1145,7 +1146,7 @@ static int gemm_fused(const fbst_plan_s* p, const float2* w, float2* bhat, int n
   if (ntiles > INT_MAX) return FBST_ERR_UNSUPPORTED;
   const int grid = kPersist ? (int)std::min<long long>(ntiles, sm_count()) : (int)ntiles;
   k_dense_tc_fused<NB, kPersist, F16><<<grid, kPersist ? 384 : 256, smem, s>>>(
-      mapA, mapW, bhat, in.B, in.N, in.L, nblk, b0, nbeam, shared_rhs ? 0 : 1, p->tc_gexp, p->tc_wpart,
+      mapA, mapW, bhat, in.B, in.N, in.L, nblk, b0, nbeam, shared_rhs ? 0 : 1, p->tc_gexp, p->tc_wmax,
       p->d_status, p->wait_ns ? p->wait_ns : kWaitNs);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
@@ -1173,9 +1174,10 @@ static bool fused_variant(const fbst_plan_s* p) {
 
 int prepare_dense_tc_scales(const fbst_plan_s* p, const float2* w, int nblk, cudaStream_t s) {
   if (variant_of(p->info.stage2) != TC_F16X3 || nblk <= 0) return FBST_OK;
-  if (!p->tc_wpart || nblk > p->band.max_blocks || nblk > 65535) return FBST_ERR_INVALID;
+  if (!p->tc_wmax || nblk > p->band.max_blocks || nblk > 65535) return FBST_ERR_INVALID;
   const size_t per_block4 = (size_t)p->info.B * p->info.L / 2;  // B x L complex64 = B L / 2 float4
-  k_tc_wparts<<<dim3(kWParts, nblk), 256, 0, s>>>(reinterpret_cast<const float*>(w), p->tc_wpart, per_block4);
+  FBST_CUDA_TRY(cudaMemsetAsync(p->tc_wmax, 0, sizeof(unsigned) * nblk, s));
+  k_tc_wmax<<<dim3(kWParts, nblk), 256, 0, s>>>(reinterpret_cast<const float*>(w), p->tc_wmax, per_block4);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
@@ -1196,11 +1198,12 @@ int launch_stage2_dense_tc_beams(const fbst_plan_s* p, const float2* w, float2* 
   return launch_fused(p, w, bhat, nblk, b0, nbeam, s);
 }
 
-int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s) {
+int launch_stage2_dense_tc(const fbst_plan_s* p, const float2* w, float2* bhat, int nblk, cudaStream_t s,
+                           bool scales_ready) {
   if (nblk <= 0) return FBST_OK;
   if (!p->Gtc) return FBST_ERR_INVALID;
   if (fused_variant(p)) {
-    FBST_TRY(prepare_dense_tc_scales(p, w, nblk, s));
+    if (!scales_ready) FBST_TRY(prepare_dense_tc_scales(p, w, nblk, s));
     return launch_fused(p, w, bhat, nblk, 0, p->info.B, s);
   }
   if (!p->ws_tc) return FBST_ERR_INVALID;

@@ -534,7 +534,7 @@ int fbst_null_launch_count(fbst_null_t n, int nblk) {
   if (!n || nblk <= 0) return 0;
   const int maxb = n->plan->band.max_blocks;
   const int chunks = (nblk + maxb - 1) / maxb;
-  return chunks * (2 + 3 + stage2_launches(n->plan));
+  return chunks * (2 + 3 + stage2_launches(n->plan, false));
 }
 
 int fbst_null_destroy(fbst_null_t n) {

@@ -176,8 +176,8 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
   // The pre-split right-hand sides of the BF16x3 and TF32 tensor-core variants.
   if (out->stage2 == FBST_STAGE2_DENSE_BF16X3 || out->stage2 == FBST_STAGE2_DENSE_TF32)
     out->workspace_bytes += c64 * (size_t)B * (((size_t)band->max_blocks + 15) / 16 * 16) * L;
-  // The partial maxima of w behind the block scales of the FP16-split variant.
-  if (out->stage2 == FBST_STAGE2_DENSE_F16X3) out->workspace_bytes += sizeof(float) * 16 * (size_t)band->max_blocks;
+  // The block maxima of w behind the block scales of the FP16-split variant.
+  if (out->stage2 == FBST_STAGE2_DENSE_F16X3) out->workspace_bytes += sizeof(unsigned) * (size_t)band->max_blocks;
   return FBST_OK;
 }
 

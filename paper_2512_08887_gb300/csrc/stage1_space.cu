@@ -13,9 +13,10 @@
 
 namespace fbst {
 
+// At least 512 threads per SM (128 registers a thread): the kernel lives on latency hiding.
 template <int P, int E, int G>
-__global__ void __launch_bounds__(G * (P / E))
-k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(G * (P / E), G * (P / E) >= 512 ? 1 : 512 / (G * (P / E)))
+k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __restrict__ tw, int max_B) {
   constexpr int T = P / E;
   constexpr int SB = fft_smem_elems<float2>(P);
   static_assert(T <= 32 || G <= 15, "named barriers 1..15, one per transform group");
@@ -23,6 +24,14 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
   const int g = threadIdx.x / T, t = threadIdx.x % T;
   float2* fbuf = sm + g * SB;
   float2* tile = sm + G * SB;  // [B][G + 1] (padded row: conflict-free column writes)
+  // Block maxima of w for the FP16-split stage 2 (only for a launch of one job that asks for them):
+  // this CTA's per-block words after the tile, zeroed here, combined into the job's at the end.
+  unsigned* wmax_s = nullptr;
+  if (jl.n == 1 && jl.job[0].wmax) {
+    wmax_s = reinterpret_cast<unsigned*>(tile + (size_t)max_B * (G + 1));
+    for (int i = threadIdx.x; i < jl.job[0].nblk; i += blockDim.x) wmax_s[i] = 0u;
+    __syncthreads();
+  }
   long long it0, it1;
   my_range(jl.total, &it0, &it1);
   int j = 0, cur_j = -1, cur_lt = -1;
@@ -88,22 +97,39 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
     }
     __syncthreads();
     float2* out = J.w + (size_t)blk * B * L + ell0;
+    float wm = 0.f;
     for (int idx = threadIdx.x; idx < B * G; idx += blockDim.x) {
       const int b = idx / G, gg = idx % G;
-      if (ell0 + gg < L) out[(size_t)b * L + gg] = tile[b * (G + 1) + gg];
+      if (ell0 + gg < L) {
+        const float2 o = tile[b * (G + 1) + gg];
+        out[(size_t)b * L + gg] = o;
+        wm = fmaxf(wm, fmaxf(fabsf(o.x), fabsf(o.y)));
+      }
+    }
+    if (wmax_s) {
+      // The block's largest |re|, |im| (the scale of the FP16-split stage 2): a warp maximum into
+      // this CTA's per-block word (non-negative floats order like their bit patterns).
+      for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(wmax_s + blk, __float_as_uint(wm));
     }
     __syncthreads();
+  }
+  if (wmax_s) {
+    // One global atomic per block this CTA touched (the CTA's items are a contiguous range).
+    for (int i = threadIdx.x; i < jl.job[0].nblk; i += blockDim.x)
+      if (wmax_s[i]) atomicMax(jl.job[0].wmax + i, wmax_s[i]);
   }
 }
 
 template <int P, int E, int G>
 static int run_space(const job_list<space_job>& jl, int max_B, const float2* tw, cudaStream_t s) {
   constexpr int T = P / E;
-  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * (G + 1));
+  const size_t wm = (jl.n == 1 && jl.job[0].wmax) ? sizeof(unsigned) * (size_t)jl.job[0].nblk : 0;
+  const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * (G + 1)) + wm;
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
   FBST_TRY(allow_max_smem(k_czt_space_ula<P, E, G>));
   const int grid = grid_for_items(jl.total, resident_ctas(k_czt_space_ula<P, E, G>, G * T, smem));
-  k_czt_space_ula<P, E, G><<<grid, G * T, smem, s>>>(jl, tw);
+  k_czt_space_ula<P, E, G><<<grid, G * T, smem, s>>>(jl, tw, max_B);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
@@ -147,7 +173,7 @@ long long space_items(const space_job& j, fft_shape sh, int) {
 
 space_job make_space_job(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk) {
   const fbst_axis_tables& ax = p->ax[0];
-  return space_job{yhat, w, ax.pre, ax.kspec, ax.post, ax.Ma, ax.Ba, p->info.L, nblk, 0};
+  return space_job{yhat, w, ax.pre, ax.kspec, ax.post, ax.Ma, ax.Ba, p->info.L, nblk, 0, nullptr};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -368,13 +394,17 @@ static int launch_space_nufft(const fbst_plan_s* p, const float2* yhat, float2* 
   }
 }
 
-int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+static int czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, unsigned* wmax, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
   if (p->nu_nf) return launch_space_nufft(p, yhat, w, nblk, s);
   if (p->geom.kind == FBST_ULA) {
     job_list<space_job> jl;
     jl.n = 1;
     jl.job[0] = make_space_job(p, yhat, w, nblk);
+    if (wmax) {
+      FBST_CUDA_TRY(cudaMemsetAsync(wmax, 0, sizeof(unsigned) * nblk, s));
+      jl.job[0].wmax = wmax;
+    }
     const fft_shape sh = space_shape(p);
     jl.total = space_items(jl.job[0], sh, p->info.P_space_x);
     return launch_space_jobs(jl, p->info.P_space_x, sh, p->ax[0].Ba, p->tw32, s);
@@ -388,6 +418,16 @@ int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nb
     case 256: return czt_space_ura_P<256>(p, yhat, w, nblk, s);
     default: return FBST_ERR_UNSUPPORTED;
   }
+}
+
+int launch_czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  return czt_space(p, yhat, w, nblk, nullptr, s);
+}
+
+int launch_czt_space_scaled(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, int blk0,
+                            cudaStream_t s) {
+  if (p->tc_wmax_stage1 && (blk0 < 0 || blk0 + nblk > p->band.max_blocks)) return FBST_ERR_INVALID;
+  return czt_space(p, yhat, w, nblk, p->tc_wmax_stage1 ? p->tc_wmax + blk0 : nullptr, s);
 }
 
 }  // namespace fbst

@@ -268,13 +268,14 @@ int launch_stage2_dense_fp32(const fbst_plan_s* p, const float2* w, float2* bhat
   return launch_dense_fp32_rhs(p, w, bhat, nblk, false, s);
 }
 
-int stage2_launches(const fbst_plan_s* p) {
+int stage2_launches(const fbst_plan_s* p, bool w_from_stage1) {
   switch (p->info.stage2) {
     case FBST_STAGE2_GS:
     case FBST_STAGE2_GS_IR1: return 1;
     case FBST_STAGE2_DENSE_FP32: return 1;
     case FBST_STAGE2_DENSE_TF32X3: return 1;  // fused: splits its operands in shared memory
-    case FBST_STAGE2_DENSE_F16X3: return 2;   // the block scales of w, then the fused GEMM
+    case FBST_STAGE2_DENSE_F16X3:  // the fused GEMM, after a pass for the block maxima of w unless
+      return w_from_stage1 && p->tc_wmax_stage1 ? 1 : 2;  // stage 1b wrote them
     default: return 2;  // other tensor-core variants: operand preparation + GEMM
   }
 }

@@ -57,8 +57,8 @@ extern "C" int fbst_execute_stream(fbst_plan_t p, const void* record, long long 
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
     FBST_TRY(launch_czt_time_record(p, rec + (size_t)c0 * hop, T, hop, p->ws_yhat, nb, s));
-    FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nb, s));
-    FBST_TRY(run_stage2(p, p->ws_w, p->stream_bhat, nb, s));
+    FBST_TRY(launch_czt_space_scaled(p, p->ws_yhat, p->ws_w, nb, 0, s));
+    FBST_TRY(run_stage2(p, p->ws_w, p->stream_bhat, nb, s, true));
     const long long total = (long long)nb * in.B * hop;
     const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, (long long)sm_count() * 8));
     k_stream_emit<<<grid, 256, 0, s>>>(p->stream_bhat, static_cast<float2*>(out), in.B, in.N, hop, c, out_len, c0, nb);

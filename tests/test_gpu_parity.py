@@ -337,3 +337,22 @@ def test_f16x3_block_scales_keep_accuracy_across_magnitudes(rng):
         else:
             err = O.rel_l2(got[i] / np.float64(m), ref[i])
             assert err < TOL_E2E, f"block scaled by {m:g}: {err:.3e}"
+
+
+@pytest.mark.parametrize("case", [("ula", 48, 1, 40, 1, 256, 0.5, 5), ("ura", 8, 8, 8, 8, 64, 0.3, 3)])
+def test_f16x3_block_scales_from_stage1_equal_separate_pass(rng, case):
+    # On a linear array the spatial chirp-z finds each block's largest |re|, |im| as it writes w, and
+    # stage 2 uses it; toeplitz_apply on the same w finds it with a pass of its own. The maximum is
+    # exact either way, so both give the same scales and bitwise the same output. (A rectangular
+    # array takes the separate pass in both.) Chunks of 2 blocks: each chunk has its own maxima.
+    kind, mx, my, bx, by, N, fbw, nblk = case
+    plan, pb = make(kind, mx, my, bx, by, N, fbw, stage2="dense_f16x3", max_blocks=2)
+    y = crandn(rng, nblk, pb.M, N)
+    a = run(plan, "execute", y, (nblk, pb.B, N), nblk)
+    w = run(plan, "czt", y, (nblk, pb.B, pb.L), nblk)
+    b = run(plan, "toeplitz_apply", w, (nblk, pb.B, N), nblk)
+    assert plan.sync_status() == 0
+    assert np.array_equal(a, b)
+    assert O.rel_l2(a, O.fbst(pb, y)) < TOL_E2E
+    chunks = (nblk + 1) // 2
+    assert plan.launch_count(nblk) == chunks * (2 + (1 if kind == "ula" else 2))
