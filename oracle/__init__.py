@@ -7,8 +7,9 @@ Parity status of each function is stated in fbst_oracle's docstrings; every func
 the tests in tests/test_oracle_pins.py except the size of the noise-free bias of a plane wave,
 which the paper gives no number for ("parity unpinned": only a sanity bound is checked). The
 beamspace interference nulling of Eq. (14) is pinned by tests/test_oracle_nulling.py, and the
-non-uniform arrays of Sec. IX (make_problem(..., offsets=...)) by tests/test_oracle_nonuniform.py, and
-the off-grid beams of Sec. VIII-A by tests/test_oracle_offgrid.py.
+non-uniform arrays of Sec. IX (make_problem(..., offsets=...)) by tests/test_oracle_nonuniform.py,
+the off-grid beams of Sec. VIII-A by tests/test_oracle_offgrid.py, and the time-domain nulling of
+Eq. (15) by tests/test_oracle_nulling_time.py.
 """
 from .fbst_oracle import (  # noqa: F401
     Problem,
@@ -36,6 +37,10 @@ from .fbst_oracle import (  # noqa: F401
     fbst_nulled_offgrid,
     NullingFactors,
     fbst_nulled,
+    F_u_interval,
+    time_interval,
+    TimeNullingFactors,
+    fbst_nulled_time,
     lstsq_augmented,
     noise_power_trace,
     delay_and_sum_exact,

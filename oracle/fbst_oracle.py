@@ -311,6 +311,74 @@ def fbst_nulled(pb: Problem, y: np.ndarray, interferers, beams=None,
     return factors.out.apply(factors.coefficients(w, w_int))
 
 
+def F_u_interval(pb: Problem, n0: int, Nu: int) -> np.ndarray:
+    """[F_u]_{n, ell} = exp(j*omega_ell*t_n) (Eq. (7)) on the samples t_n = n0 .. n0 + Nu - 1,
+    shape (Nu, L); n0 = 0, Nu = N is the block's own F_u."""
+    n = n0 + np.arange(Nu, dtype=np.float64)
+    return np.exp(TWO_PI_J * pb.epsilon * np.multiply.outer(n, pb.lprime) / pb.L)
+
+
+def time_interval(pb: Problem) -> tuple:
+    """The broader reconstruction interval of the time-domain nulling (Eq. (15)): L samples centred
+    on the block, t = -(L - N)/2 .. (L + N)/2 - 1, so that its F_u is square (full column rank)."""
+    return -((pb.L - pb.N) // 2), pb.L
+
+
+class TimeNullingFactors:
+    """Eq. (15): the nulled time-domain beam y~_b = y_b - sum_p G'_{b,p} y_p, windowed to the block,
+    with y_b = F_u beta_b the plain beam over the block's N samples, y_p = F_x beta_p the interferer
+    beam over the broader interval (F_x = F_u on that interval), and
+    G'_{b,p} = F_u H_{b,p} F_x^+,   H_{b,p} = (F_b^H F_b + delta I)^{-1} F_b^H F_p.
+    The matrices are formed literally: F_x^+ by the pseudo-inverse, H by a dense solve."""
+
+    def __init__(self, pb: Problem, interferers, beams=None, n0: int | None = None, Nu: int | None = None):
+        self.pb = pb
+        self.interferers = [int(p) for p in interferers]
+        d0, dN = time_interval(pb)
+        self.n0, self.Nu = (d0 if n0 is None else int(n0)), (dN if Nu is None else int(Nu))
+        self.Fx = F_u_interval(pb, self.n0, self.Nu)                   # (Nu, L)
+        self.Fx_pinv = np.linalg.pinv(self.Fx)                         # (L, Nu)
+        self.out = Stage2Factors(pb, beams)
+        self.intf = Stage2Factors(pb, self.interferers)
+        Fu = F_u(pb)
+        self.Gp = []
+        for b in self.out.beams:
+            A = gram(pb, int(b))
+            row = []
+            for p in self.interferers:
+                H = scipy.linalg.solve(A, cross_gram(pb, int(b), p))  # (L, L)
+                row.append(Fu @ H @ self.Fx_pinv)                      # (N, Nu)
+            self.Gp.append(row)
+
+    def interferer_beams(self, w_int: np.ndarray) -> np.ndarray:
+        """The interferers' time-domain beams over the broader interval, F_x A_p^{-1} w_p:
+        (nblk, P, L) -> (nblk, P, Nu)."""
+        beta = self.intf.coefficients(w_int)
+        return np.einsum("nl,bpl->bpn", self.Fx, beta)
+
+    def apply(self, y: np.ndarray, y_int: np.ndarray) -> np.ndarray:
+        """Eq. (15) on time-domain beams: y (nblk, nbeams, N), y_int (nblk, P, Nu) -> y~."""
+        out = np.array(y, dtype=np.complex128)
+        for i in range(len(self.out.beams)):
+            for j in range(len(self.interferers)):
+                out[:, i, :] -= np.asarray(y_int[:, j, :], dtype=np.complex128) @ self.Gp[i][j].T
+        return out
+
+
+def fbst_nulled_time(pb: Problem, y: np.ndarray, interferers, beams=None,
+                     factors: TimeNullingFactors | None = None) -> np.ndarray:
+    """FBST followed by the time-domain nulling of Eq. (15): y (nblk, M, N) -> y~ (nblk, nbeams, N)."""
+    y = np.asarray(y)
+    if y.ndim == 2:
+        y = y[None]
+    if factors is None:
+        factors = TimeNullingFactors(pb, interferers, beams)
+    w = fan_coefficients(pb, y, factors.out.beams)
+    plain = factors.out.apply(w)
+    w_int = fan_coefficients(pb, y, factors.interferers)
+    return factors.apply(plain, factors.interferer_beams(w_int))
+
+
 # ----------------------------------------------------------------------------------------------
 # Off-grid beams by interpolation of beam vectors (Sec. VIII-A)
 # ----------------------------------------------------------------------------------------------
