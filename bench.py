@@ -10,7 +10,7 @@ accumulation (FP32-class: its error against the FP64 oracle is measured and repo
 CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|OG|STREAM] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|C2NT|OG|STREAM] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
 stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
@@ -403,9 +403,13 @@ def null_roofline(B: int, L: int, P: int, nblk: int, ms: float, contraction: str
 
 def run_null(args) -> None:
     """C2N: the transform of the C2 array with beamspace nulling (Eq. (14)) of grid beams 64 and 96,
-    64 blocks per step; one step = fbst_null_execute (stage 1, the bracket of Eq. (14), stage 2)."""
+    64 blocks per step; one step = fbst_null_execute (stage 1, the bracket of Eq. (14), stage 2).
+    C2NT: the same scene with the time-domain form (Eq. (15)); one step = fbst_null_execute of a
+    time-domain object (stage 1, the plain stage 2, the interferers' beams over the broader interval,
+    the time-domain subtraction)."""
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        raise SystemExit("--workload C2N runs on one GPU (replicas of it scale like C2)")
+        raise SystemExit("--workload C2N/C2NT runs on one GPU (replicas of it scale like C2)")
+    time_form = args.workload == "C2NT"
     import torch
     import paper_2512_08887_gb300 as fb
     from paper_2512_08887_gb300.build import build
@@ -424,7 +428,7 @@ def run_null(args) -> None:
     info = plan.info
     L = info.L
     t0 = time.perf_counter()
-    nl = fb.Nulling(plan, ints, args.contraction)
+    nl = fb.Nulling(plan, ints, args.contraction, time_domain=time_form)
     t_create = time.perf_counter() - t0
     y = torch.from_numpy(d["y"]).to(dev)
     out = torch.empty((nblk, B, N), dtype=torch.complex64, device=dev)
@@ -437,7 +441,7 @@ def run_null(args) -> None:
     pb = O.make_problem("ula", M, 1, B, 1, N, frac_bw=info.fb_num / info.fb_den, epsilon=info.eps_num / info.eps_den,
                         delta=info.delta, L=L)
     got = out[:2].cpu().numpy()[:, beams]
-    ref = O.fbst_nulled(pb, d["y"][:2], ints, beams=beams)
+    ref = (O.fbst_nulled_time if time_form else O.fbst_nulled)(pb, d["y"][:2], ints, beams=beams)
     rel_err = O.rel_l2(got, ref)
     # Nulling subtracts large corrections: FP32 errors follow the input scale, so the error is also
     # given relative to the plain transform's output of the same blocks and beams.
@@ -470,6 +474,12 @@ def run_null(args) -> None:
     wbuf = torch.empty((nblk, B, L), dtype=torch.complex64, device=dev)
     wt = torch.empty_like(wbuf)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(kin)]
+    if time_form:
+        # The time-domain subtraction alone needs the interferers' beams over the broader interval:
+        # the oracle's, rounded to complex64 (untimed set-up).
+        tf = O.TimeNullingFactors(pb, ints, beams=[])
+        y_int = torch.from_numpy(tf.interferer_beams(O.fan_coefficients(pb, d["y"], ints)).astype(np.complex64)).to(dev)
+        plain = torch.empty_like(out)
     for i in range(kin):
         flush.zero_()
         ev[i][0].record(stream)
@@ -477,12 +487,18 @@ def run_null(args) -> None:
         ev[i][1].record(stream)
         plan.czt_space(yhat, wbuf, nblk)
         ev[i][2].record(stream)
-        nl.apply(wbuf, wt, nblk)
-        ev[i][3].record(stream)
-        plan.toeplitz_apply(wt, out, nblk)
+        if time_form:
+            plan.toeplitz_apply(wbuf, plain, nblk)
+            ev[i][3].record(stream)
+            nl.apply_time(plain, y_int, out, nblk)
+        else:
+            nl.apply(wbuf, wt, nblk)
+            ev[i][3].record(stream)
+            plan.toeplitz_apply(wt, out, nblk)
         ev[i][4].record(stream)
     torch.cuda.synchronize()
-    names = ["czt_time", "czt_space", "null_bracket", "stage2"]
+    names = ["czt_time", "czt_space", "stage2", "null_time_apply"] if time_form else \
+        ["czt_time", "czt_space", "null_bracket", "stage2"]
     kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
 
     # End to end through the public API: pinned host input copied in, the nulled transform, the
@@ -503,25 +519,34 @@ def run_null(args) -> None:
 
     peaks, peak_kind = load_peaks()
     fp32 = measure_fp32_peak(fb, 0)
-    roofs = {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32) for k, v in kern_ms.items() if k != "null_bracket"}
-    roofs["null_bracket"] = null_roofline(B, L, P, nblk, kern_ms["null_bracket"], args.contraction, peaks, peak_kind,
-                                          fp32)
+    roofs = {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32) for k, v in kern_ms.items()
+             if k not in ("null_bracket", "null_time_apply")}
+    if time_form:
+        # F_x^{-1} per interferer, the cross Gram contraction (the bracket's shape), the plan's
+        # stage 2 of the correction and the subtraction: reported against the contraction's roof,
+        # as the bracket of Eq. (14) is.
+        roofs["null_time_apply"] = null_roofline(B, L, P, nblk, kern_ms["null_time_apply"], args.contraction, peaks,
+                                                 peak_kind, fp32)
+    else:
+        roofs["null_bracket"] = null_roofline(B, L, P, nblk, kern_ms["null_bracket"], args.contraction, peaks,
+                                              peak_kind, fp32)
     dom = max(kern_ms, key=kern_ms.get)
 
     cpu = None
     if not args.no_cpu_baseline:
         sb = [int(b) for b in np.linspace(0, B - 1, 32).astype(int)]
         t0 = time.perf_counter()
-        fac = O.NullingFactors(pb, ints, sb)
+        fac = (O.TimeNullingFactors if time_form else O.NullingFactors)(pb, ints, sb)
         t_fac = time.perf_counter() - t0
         done, t_exec = 0, 0.0
         while t_exec < 10.0 or done == 0:
             t0 = time.perf_counter()
-            O.fbst_nulled(pb, d["y"][:4], ints, factors=fac)
+            (O.fbst_nulled_time if time_form else O.fbst_nulled)(pb, d["y"][:4], ints, factors=fac)
             t_exec += time.perf_counter() - t0
             done += 1
         cpu = {"value": done * 4 * len(sb) * N / t_exec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{done} x (4 blocks x 32 of {B} beams) of C2N, FP64 numpy oracle of Eq. (14), "
+               "sample": f"{done} x (4 blocks x 32 of {B} beams) of {args.workload}, FP64 numpy oracle of "
+                         f"Eq. ({15 if time_form else 14}), "
                          f"per-plan factors and cross Gram matrices ({t_fac:.1f} s) excluded"}
 
     line = {
@@ -530,8 +555,10 @@ def run_null(args) -> None:
         "dtype": f"f32 stage 1, {args.contraction} nulling contraction with FP64 interferer solves, "
                  f"{fb.STAGE2_NAMES[info.stage2]} stage 2",
         "data": "synthetic",
-        "config": {"workload": f"C2N: ULA M={M} B={B} N={N} L={L} fb={c['frac_bw']}, beamspace nulling (Eq. (14)) "
-                               f"of grid beams {ints}, {nblk} blocks/step, complex64",
+        "config": {"workload": (f"C2NT: ULA M={M} B={B} N={N} L={L} fb={c['frac_bw']}, time-domain nulling "
+                                f"(Eq. (15)) of grid beams {ints}, {nblk} blocks/step, complex64") if time_form else
+                               (f"C2N: ULA M={M} B={B} N={N} L={L} fb={c['frac_bw']}, beamspace nulling (Eq. (14)) "
+                                f"of grid beams {ints}, {nblk} blocks/step, complex64"),
                    "M": M, "B": B, "N": N, "L": L, "interferers": ints, "nblk_per_gpu": nblk,
                    "stage2": fb.STAGE2_NAMES[info.stage2], "contraction": args.contraction,
                    "l2": "flushed before every timed step (256 MiB write, untimed)", "parallelism": "replicas x1"},
@@ -815,29 +842,33 @@ def run_stream(args) -> None:
 
 
 def run_reference_null(args) -> None:
-    """Reference arm of C2N: the FP64 oracle of Eq. (14) on one block x 16 beams per step."""
+    """Reference arm of C2N (C2NT): the FP64 oracle of Eq. (14) (Eq. (15)) on one block x 16 beams per
+    step."""
     import oracle as O
     from synth import configs
     c = configs.NULLING["C2N"]
     y = configs.nulling_data("C2N", nblk=1)["y"]
     beams = [int(b) for b in np.linspace(0, c["bx"] - 1, 16).astype(int)]
     pb = O.make_problem("ula", c["mx"], 1, c["bx"], 1, c["N"], frac_bw=c["frac_bw"], epsilon=1.01, delta_rel=1e-3)
-    fac = O.NullingFactors(pb, c["interferers"], beams)
+    tform = args.workload == "C2NT"
+    fac = (O.TimeNullingFactors if tform else O.NullingFactors)(pb, c["interferers"], beams)
+    run = O.fbst_nulled_time if tform else O.fbst_nulled
     for _ in range(args.warmup):
-        O.fbst_nulled(pb, y, c["interferers"], factors=fac)
+        run(pb, y, c["interferers"], factors=fac)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.fbst_nulled(pb, y, c["interferers"], factors=fac)
+        run(pb, y, c["interferers"], factors=fac)
         times.append(time.perf_counter() - t0)
     value = len(beams) * c["N"] * len(times) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "C2N oracle sample", "M": c["mx"], "N": c["N"], "B": c["bx"],
+            "config": {"workload": f"{args.workload} oracle sample", "M": c["mx"], "N": c["N"], "B": c["bx"],
                        "interferers": c["interferers"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "per step: 1 block x 16 beams of C2N (FP64 numpy oracle of Eq. (14), "
+                             "sample": f"per step: 1 block x 16 beams of {args.workload} (FP64 numpy oracle of "
+                                       f"Eq. ({15 if tform else 14}), "
                                        "per-plan factors and cross Gram matrices excluded)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -874,7 +905,7 @@ def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload == "C2N":
+    if args.workload in ("C2N", "C2NT"):
         run_reference_null(args)
         return
     if args.workload == "OG":
@@ -944,7 +975,7 @@ def main() -> None:
     if args.workload == "C5":
         run_c5(args)
         return
-    if args.workload == "C2N":
+    if args.workload in ("C2N", "C2NT"):
         run_null(args)
         return
     if args.workload == "OG":

@@ -406,6 +406,31 @@ int fbst_null_create(fbst_null_t* out, fbst_plan_t p, const int* interferers, in
 int fbst_null_create_directions(fbst_null_t* out, fbst_plan_t p, const double* directions, int P, int K,
                                 int contraction, void* stream);
 
+/* The time-domain form of the nulling (Sec. VIII-B, Eq. (15)) for P grid interferer beams: each
+ * interferer's beam y_p = F_x A_p^{-1} w_p over a broader reconstruction interval, the 2L samples
+ * t = -(2L - N)/2 .. (2L + N)/2 - 1 centred on the block (F_x = F_u of Eq. (7) on that interval, of
+ * full column rank and well conditioned; an interval of only L samples is square but numerically
+ * singular for L in the hundreds), is mapped by G'_{b,p} = F_u H_{b,p} F_x^+,
+ * H_{b,p} = A_b^{-1} F_b^H F_p, and subtracted from the plain beam y_b over the block's N samples.
+ * The object holds, built in FP64: the cross Gram matrices F_b^H F_p ([B][L][P*L], complex64),
+ * F_x A_p^{-1} ([P][2L][L], kept in FP64; the interferers' beams are summed from it in FP64, since
+ * its entries are of the size of ||A_p^{-1}|| and cancel down to the beam) and
+ * F_x^+ = (F_x^H F_x)^{-1} F_x^H ([P][L][2L], complex64); G'_{b,p} is applied factor by factor (F_x^+,
+ * the cross Gram contraction, the plan's stage 2). With F_x of full column rank the result equals
+ * Eq. (14) up to rounding. Requires N even and L <= 1024 (FBST_ERR_UNSUPPORTED otherwise); device
+ * memory 8*B*L*P*L + 48*P*L*L bytes plus 8*max_blocks*(3*P*L + B*L + B*N) of workspace. Otherwise
+ * as fbst_null_create; fbst_null_apply is FBST_ERR_UNSUPPORTED on such an object, fbst_null_execute
+ * runs the time-domain form. */
+int fbst_null_create_time(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction,
+                          void* stream);
+
+/* Eq. (15) on time-domain beams (an object of fbst_null_create_time): y (device, [nblk][B][N], the
+ * plain beams over each block) and y_int (device, [nblk][P][2L], the interferers' beams over the
+ * broader interval, in the order of the object's interferers) -> out (device, [nblk][B][N]),
+ * out_b = y_b - sum_p G'_{b,p} y_p. out may equal y. Asynchronous on `stream`; pointers 16-byte
+ * aligned (else FBST_ERR_INVALID). FBST_ERR_UNSUPPORTED on an object of the other forms. */
+int fbst_null_apply_time(fbst_null_t n, const void* y, const void* y_int, void* out, int nblk, void* stream);
+
 /* The bracket of Eq. (14) alone: w (device, [nblk][B][L], as fbst_czt writes it) ->
  * wt (device, [nblk][B][L]), wt_b = w_b - sum_j F_b^H F_{p_j} A_{p_j}^{-1} w_{p_j}. wt may equal w
  * (in place); otherwise the two must not overlap. Asynchronous on `stream`; both pointers 16-byte

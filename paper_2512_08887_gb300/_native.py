@@ -86,6 +86,8 @@ SIGNATURES = {
     "fbst_get_shapes": (_I, [_VP, C.POINTER(_I)]),
     "fbst_null_create": (_I, [C.POINTER(_VP), _VP, C.POINTER(_I), _I, _I, _VP]),
     "fbst_null_create_directions": (_I, [C.POINTER(_VP), _VP, C.POINTER(C.c_double), _I, _I, _I, _VP]),
+    "fbst_null_create_time": (_I, [C.POINTER(_VP), _VP, C.POINTER(_I), _I, _I, _VP]),
+    "fbst_null_apply_time": (_I, [_VP, _VP, _VP, _VP, _I, _VP]),
     "fbst_null_apply": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_null_execute": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fbst_null_launch_count": (_I, [_VP, _I]),
@@ -400,16 +402,25 @@ class Batch:
 
 class Nulling:
     """Beamspace interference nulling of grid beams `interferers` for `plan` (Eq. (14);
-    fbst_null_create / fbst_null_destroy). The plan must outlive this object. `contraction`: "fp32"
+    fbst_null_create / fbst_null_destroy), or its time-domain form (Eq. (15), time_domain=True;
+    fbst_null_create_time). The plan must outlive this object. `contraction`: "fp32"
     (CUDA cores, the accurate one: the correction is about ten times the nulled result at 20 dB, so
     its product rounding matters) or "tf32x3" (tensor cores, faster, coarser products)."""
 
     def __init__(self, plan: Plan, interferers=None, contraction: str = "fp32", stream=None, directions=None,
-                 K: int = 8):
+                 K: int = 8, time_domain: bool = False):
         self._lib = load_library()
         self.plan = plan
+        self.time_domain = bool(time_domain)
         h = C.c_void_p()
-        if directions is not None:
+        if time_domain:
+            # The time-domain form of Eq. (15) (grid interferers).
+            self.interferers = [int(p) for p in interferers]
+            arr = (C.c_int * max(1, len(self.interferers)))(*self.interferers)
+            _check(self._lib.fbst_null_create_time(C.byref(h), plan._h, arr, len(self.interferers),
+                                                   NULL_CONTRACTION[contraction], _stream(stream)),
+                   "fbst_null_create_time")
+        elif directions is not None:
             # Off-grid interferers: (u, v) direction cosines, vectors interpolated from K grid beams.
             dirs = [(float(d[0]), float(d[1]) if len(d) > 1 else 0.0) for d in directions]
             self.interferers = dirs
@@ -432,6 +443,13 @@ class Nulling:
         """Nulled transform: y [nblk][M][N] -> bhat [nblk][B][N], complex64 device buffers."""
         _check(self._lib.fbst_null_execute(self._h, _ptr(y), _ptr(bhat), int(nblk), _stream(stream)),
                "fbst_null_execute")
+
+    def apply_time(self, y, y_int, out, nblk: int, stream=None) -> None:
+        """Eq. (15) on time-domain beams (time_domain=True): y [nblk][B][N] plain beams, y_int
+        [nblk][P][2L] the interferers' beams over the broader interval of 2L samples centred on the
+        block -> out [nblk][B][N]."""
+        _check(self._lib.fbst_null_apply_time(self._h, _ptr(y), _ptr(y_int), _ptr(out), int(nblk), _stream(stream)),
+               "fbst_null_apply_time")
 
     def launch_count(self, nblk: int) -> int:
         return int(self._lib.fbst_null_launch_count(self._h, int(nblk)))

@@ -31,8 +31,20 @@
 //   theta_axis = 2*pi*rho*[(u_b - u_p)/fb + eps*(ell'*u_b - k'*u_p)/L]
 // with u the beam's direction cosine along that axis and D_N(x) = sum_{n<N} exp(i*x*n). For b = p it
 // is the Toeplitz A_b - delta I of Sec. V; for b != p the carriers no longer cancel.
+//
+// The time-domain form (Eq. (15)) works on time-domain beams: out_b = y_b - sum_j G'_{b,j} y_j with
+// y_j = F_x A_{p_j}^{-1} w_{p_j} the interferer's beam over a broader interval of 2L samples (F_x
+// of full column rank and well conditioned there) and G'_{b,j} = F_u A_b^{-1} (F_b^H F_{p_j}) F_x^+,
+// applied factor by factor at run time: F_x^+ (per interferer, FP32 CUDA cores), the contraction
+// above with the cross Gram matrices in place of G_{b,j}, the plan's stage 2, and a subtraction.
+// Plan time: the cross Gram rows (k_null_G without the apply); F_x A_{p_j}^{-1} (k_null_rows_gs,
+// FP64 Gohberg-Semencul on the rows of F_x, kept in FP64: the interferers' beams over the broader
+// interval are summed from it in FP64 by k_null_yext64); and F_x^+ = T^{-1} F_x^H with the
+// Hermitian Toeplitz T = F_x^H F_x, whose Levinson column is computed on the host in FP64 and whose
+// inverse is applied to the rows of F_x by the same FP64 Gohberg-Semencul kernel.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -156,7 +168,8 @@ template <int PG> struct gs64_e { static constexpr int value = PG >= 2048 ? 16 :
 // product r A^{-1} with A Hermitian is conj(A^{-1} conj(r)): the row of the cross Gram matrix is
 // conjugated, taken through the FP64 Gohberg-Semencul apply of A_{p_j}^{-1} and conjugated back.
 // One CTA per (ell, b, j).
-template <int PG>
+// APPLY = false stores the cross Gram matrix F_b^H F_{p_j} itself (the time-domain form of Eq. (15)).
+template <int PG, bool APPLY>
 __global__ void __launch_bounds__(PG / gs64_e<PG>::value)
 k_null_G(const double2* __restrict__ XV64, float2* __restrict__ Gn, const __grid_constant__ null_consts c,
          const double2* __restrict__ tw) {
@@ -172,7 +185,7 @@ k_null_G(const double2* __restrict__ XV64, float2* __restrict__ Gn, const __grid
     X[r] = Xj[i];
     Vv[r] = Xj[PG + i];
   }
-  gs_apply<PG, E>(v, X, Vv, sm64, tw, t, L);
+  if constexpr (APPLY) gs_apply<PG, E>(v, X, Vv, sm64, tw, t, L);
   float2* row = Gn + ((size_t)b * L + ell) * PL + (size_t)j * L;
 #pragma unroll
   for (int r = 0; r < E; ++r) {
@@ -181,27 +194,101 @@ k_null_G(const double2* __restrict__ XV64, float2* __restrict__ Gn, const __grid
   }
 }
 
+// Gx[j][n][k] = (R A_j^{-1})[n, k] for the FP64 rows R [nrows][L] (row n through the same
+// conjugate Gohberg-Semencul apply as k_null_G, with the spectra of A_j), kept in FP64. One CTA
+// per (n, j).
 template <int PG>
-int build_G_P(const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, cudaStream_t s) {
+__global__ void __launch_bounds__(PG / gs64_e<PG>::value)
+k_null_rows_gs(const double2* __restrict__ XV64, const double2* __restrict__ R, double2* __restrict__ Gx, int L,
+               int nrows, const double2* __restrict__ tw) {
+  constexpr int E = gs64_e<PG>::value, T = PG / E;
+  extern __shared__ double2 sm64[];
+  const int n = blockIdx.x, j = blockIdx.z, t = threadIdx.x;
+  const double2* Xj = XV64 + (size_t)j * 2 * PG;
+  double2 v[E], X[E], Vv[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = t + T * r;
+    v[r] = i < L ? cconj(R[(size_t)n * L + i]) : make_double2(0.0, 0.0);
+    X[r] = Xj[i];
+    Vv[r] = Xj[PG + i];
+  }
+  gs_apply<PG, E>(v, X, Vv, sm64, tw, t, L);
+  double2* row = Gx + ((size_t)j * nrows + n) * L;
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = t + T * r;
+    if (i < L) row[i] = cconj(v[r]);
+  }
+}
+
+// The interferers' beams over the broader interval, yext[blk][j][n] = sum_k Gx[j][n][k] w[blk][p_j][k],
+// accumulated in FP64 and rounded once: Gx = F_x A_{p_j}^{-1} has entries of the size of
+// ||A^{-1}|| whose products cancel down to the much smaller beam, so an FP32 sum would lose that
+// factor. One warp per (n, j) and 8 blocks; lanes split k, then a warp sum.
+__global__ void k_null_yext64(const double2* __restrict__ Gx, const float2* __restrict__ w, float2* __restrict__ yext,
+                              const __grid_constant__ null_consts c, int B, int nb, int Nu) {
+  constexpr int KB = 8;
+  const int n = blockIdx.x, j = blockIdx.y, blk0 = blockIdx.z * KB, lane = threadIdx.x, L = c.L;
+  const double2* g = Gx + ((size_t)j * Nu + n) * L;
+  double2 acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int k = lane; k < L; k += 32) {
+    const double2 gk = g[k];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      if (blk0 + q < nb) {
+        const float2 x = w[((size_t)(blk0 + q) * B + c.ip[j]) * L + k];
+        acc[q].x += gk.x * x.x - gk.y * x.y;
+        acc[q].y += gk.x * x.y + gk.y * x.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KB; ++q) {
+    double re = acc[q].x, im = acc[q].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0 && blk0 + q < nb) yext[((size_t)(blk0 + q) * c.P + j) * Nu + n] = make_float2((float)re, (float)im);
+  }
+}
+
+template <int PG>
+int build_G_P(const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, bool apply,
+              const double2* rows, int nrows, double2* Gx, cudaStream_t s) {
   constexpr int E = gs64_e<PG>::value;
   const size_t smem = 2 * sizeof(double2) * fft_smem_elems<double2>(PG);
-  FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_G<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_null_G<PG><<<dim3(c.L, B, c.P), PG / E, smem, s>>>(XV64, Gn, c, tw);
+  if (rows) {
+    FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_rows_gs<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_null_rows_gs<PG><<<dim3(nrows, 1, c.P), PG / E, smem, s>>>(XV64, rows, Gx, c.L, nrows, tw);
+  } else if (apply) {
+    FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_G<PG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_null_G<PG, true><<<dim3(c.L, B, c.P), PG / E, smem, s>>>(XV64, Gn, c, tw);
+  } else {
+    FBST_CUDA_TRY(cudaFuncSetAttribute(k_null_G<PG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_null_G<PG, false><<<dim3(c.L, B, c.P), PG / E, smem, s>>>(XV64, Gn, c, tw);
+  }
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
-int build_G(int PG, const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, cudaStream_t s) {
+// Eq. (14)'s G_{b,j} (apply), the cross Gram matrices alone (!apply), or with `rows` the FP64
+// products rows x A_j^{-1} (nrows rows, c.P matrices A_j given by the spectra XV64) into Gx.
+int build_G(int PG, const double2* XV64, float2* Gn, const null_consts& c, int B, const double2* tw, cudaStream_t s,
+            bool apply = true, const double2* rows = nullptr, int nrows = 0, double2* Gx = nullptr) {
   switch (PG) {
-    case 16: return build_G_P<16>(XV64, Gn, c, B, tw, s);
-    case 32: return build_G_P<32>(XV64, Gn, c, B, tw, s);
-    case 64: return build_G_P<64>(XV64, Gn, c, B, tw, s);
-    case 128: return build_G_P<128>(XV64, Gn, c, B, tw, s);
-    case 256: return build_G_P<256>(XV64, Gn, c, B, tw, s);
-    case 512: return build_G_P<512>(XV64, Gn, c, B, tw, s);
-    case 1024: return build_G_P<1024>(XV64, Gn, c, B, tw, s);
-    case 2048: return build_G_P<2048>(XV64, Gn, c, B, tw, s);
-    case 4096: return build_G_P<4096>(XV64, Gn, c, B, tw, s);
+    case 16: return build_G_P<16>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 32: return build_G_P<32>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 64: return build_G_P<64>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 128: return build_G_P<128>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 256: return build_G_P<256>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 512: return build_G_P<512>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 1024: return build_G_P<1024>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 2048: return build_G_P<2048>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
+    case 4096: return build_G_P<4096>(XV64, Gn, c, B, tw, apply, rows, nrows, Gx, s);
     default: return FBST_ERR_UNSUPPORTED;
   }
 }
@@ -264,6 +351,63 @@ int stream_grid(long long items, int threads) {
 
 bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
+// Time-domain form (Eq. (15)): F_x[n][ell] = exp(i*omega_ell*t_n) on the broader interval of
+// Nu = 2L samples t_n = n0 + n, n0 = -(2L - N)/2, in FP64 on the host, the phase eps*ell'*t/L
+// reduced exactly (2*en*ell'*t modulo 2*ed*L in units of pi/(ed*L)). Twice the basis size keeps
+// F_x well conditioned (its frequencies span 1.01 cycles per sample and interleave near half a
+// cycle, which an interval of L samples cannot resolve).
+void time_rows(const fbst_info& in, std::vector<std::complex<double>>& F) {
+  const int L = in.L, Nu = 2 * L, n0 = -(Nu - in.N) / 2;
+  const int64_t D = in.eps_den * (int64_t)L;
+  F.assign((size_t)Nu * L, {0.0, 0.0});
+  for (int n = 0; n < Nu; ++n)
+    for (int ell = 0; ell < L; ++ell) {
+      const int64_t lp = (int64_t)ell + 1 - L / 2, t = (int64_t)n0 + n;
+      int64_t q = (2 * in.eps_num * lp * t) % (2 * D);
+      if (q < 0) q += 2 * D;
+      const double ang = M_PI * (double)q / (double)D;
+      F[(size_t)n * L + ell] = {std::cos(ang), std::sin(ang)};
+    }
+}
+
+// First row a(d) = sum_n exp(2*pi*i*eps*d*t_n/L), d < L, of the Gram matrix T = F_x^H F_x
+// (Hermitian Toeplitz, T[l][k] = a(k - l)), as an FP64 direct sum with the same exact reduction.
+void time_gram_row(const fbst_info& in, std::vector<std::complex<double>>& a) {
+  const int L = in.L, Nu = 2 * L, n0 = -(Nu - in.N) / 2;
+  const int64_t D = in.eps_den * (int64_t)L;
+  a.assign(L, {0.0, 0.0});
+  for (int d = 0; d < L; ++d) {
+    std::complex<double> acc = 0.0;
+    for (int n = 0; n < Nu; ++n) {
+      int64_t q = (2 * in.eps_num * (int64_t)d * ((int64_t)n0 + n)) % (2 * D);
+      if (q < 0) q += 2 * D;
+      const double ang = M_PI * (double)q / (double)D;
+      acc += std::complex<double>(std::cos(ang), std::sin(ang));
+    }
+    a[d] = acc;
+  }
+}
+
+// x = T^{-1} e_0 for the Hermitian positive definite Toeplitz T with first row a, by the Levinson
+// recursion in FP64 (first column c[d] = conj(a(d)); f_k solves T_k f_k = e_0 and extends as
+// f_{k+1}[i] = (f_k[i] - e_k conj(f_k[k-i])) / (1 - |e_k|^2), e_k = sum_{i<k} c[k-i] f_k[i]).
+bool levinson_host(const std::vector<std::complex<double>>& a, std::vector<std::complex<double>>& f) {
+  const int L = (int)a.size();
+  if (!(a[0].real() > 0.0)) return false;
+  f.assign(L, {0.0, 0.0});
+  f[0] = 1.0 / std::conj(a[0]);
+  std::vector<std::complex<double>> g(L);
+  for (int k = 1; k < L; ++k) {
+    std::complex<double> e = 0.0;
+    for (int i = 0; i < k; ++i) e += std::conj(a[k - i]) * f[i];
+    const double den = 1.0 - std::norm(e);
+    if (!(den > 0.0)) return false;
+    for (int i = 0; i <= k; ++i) g[i] = (f[i] - e * std::conj(f[k - i])) / den;
+    for (int i = 0; i <= k; ++i) f[i] = g[i];
+  }
+  return true;
+}
+
 }  // namespace
 }  // namespace fbst
 
@@ -283,11 +427,20 @@ struct fbst_null_s {
   int Kx, Ky;
   int2* ifirst;          // [P]
   float* iwts;           // [P][Kx + Ky]
+  // Time-domain form (Eq. (15)); then Q holds the cross Gram matrices F_b^H F_{p_j} themselves.
+  int time_form;
+  fbst_plan_s shx;       // descriptor of the per-interferer products F_x^+ y_j (B := P, N := L, L := 2L)
+  double2* Gx;           // [P][2L][L] F_x A_{p_j}^{-1} (FP64): an interferer's beam over the broader interval
+  float2* Xrep;          // [P][L][2L] F_x^+ = (F_x^H F_x)^{-1} F_x^H, once per interferer
+  float2* yext;          // [max_blocks][P][2L] interferer beams over the broader interval
+  float2* bh;            // [max_blocks][P][L] F_x^{-1} yext
+  float2* tmp;           // [max_blocks][B][N] the correction in the time domain
 };
 
 // The object's blocks go back through the plan's allocator (they are in the plan's registry).
 static void free_null(fbst_null_s* n) {
-  void* ptrs[] = {n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr, n->ifirst, n->iwts};
+  void* ptrs[] = {n->Q, n->shadow.Gtc, n->XV64, n->rhs, n->corr, n->ifirst, n->iwts, n->Gx, n->Xrep, n->yext,
+                  n->bh, n->tmp};
   for (void* q : ptrs) plan_free(n->plan, q);
 }
 
@@ -320,10 +473,32 @@ static int null_chunk(fbst_null_s* n, const float2* w, float2* wt, int nb, cudaS
   return FBST_OK;
 }
 
+// One chunk of Eq. (15) on time-domain beams: out = y - sum_j G'_{b,j} yext_j with
+// G'_{b,j} = F_u A_b^{-1} (F_b^H F_{p_j}) F_x^{-1}, applied factor by factor: bh_j = F_x^{-1} yext_j,
+// corr_b = sum_j (F_b^H F_{p_j}) bh_j (the contraction of Eq. (14)'s shape with the cross Gram
+// matrices), tmp = the plan's stage 2 of corr, out = y - tmp. y [nb][B][N], yext [nb][P][L]; out may
+// be y.
+static int time_chunk(fbst_null_s* n, const float2* y, const float2* yext, float2* out, int nb, cudaStream_t s) {
+  fbst_plan_s* p = n->plan;
+  const fbst_info& in = p->info;
+  n->shx.G = n->Xrep;
+  FBST_TRY(launch_dense_fp32_rhs(&n->shx, yext, n->bh, nb, false, s));
+  n->shadow.wait_ns = p->wait_ns;
+  FBST_TRY(n->contraction == FBST_NULL_TF32X3 ? launch_dense_tc_shared_rhs(&n->shadow, n->bh, n->corr, nb, s)
+                                              : launch_dense_fp32_rhs(&n->shadow, n->bh, n->corr, nb, true, s));
+  FBST_TRY(run_stage2(p, n->corr, n->tmp, nb, s));
+  const long long n4 = (long long)nb * in.B * in.N / 2;
+  k_null_sub<<<stream_grid(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(y),
+                                                  reinterpret_cast<const float4*>(n->tmp),
+                                                  reinterpret_cast<float4*>(out), n4);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
 // The nulling object of P interferers: grid beams `interferers`, or directions `dirs` ([P][2]
 // direction cosines, interpolated from K grid beams per axis) when interferers is null.
 static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers, const double* dirs, int K, int P,
-                       int contraction, void* stream) {
+                       int contraction, void* stream, bool time_form = false) {
   if (!out) return FBST_ERR_INVALID;
   *out = nullptr;
   if (!p || (!interferers && !dirs) || P < 1 || P > kMaxInterferers) return FBST_ERR_INVALID;
@@ -363,6 +538,9 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
     if (4.0L * in.eps_den * L * in.N >= lim) return FBST_ERR_UNSUPPORTED;
   }
   if (contraction == FBST_NULL_TF32X3 && ((size_t)P * L) % 8 != 0) return FBST_ERR_UNSUPPORTED;
+  // Time-domain form: grid interferers, an interval of 2L samples centred on the block (N even:
+  // the interval's start is an integer and the subtraction runs on complex pairs), L <= 1024.
+  if (time_form && (!interferers || in.N % 2 != 0 || L > 1024)) return FBST_ERR_UNSUPPORTED;
 
   fbst_null_s* n = new (std::nothrow) fbst_null_s();
   if (!n) return FBST_ERR_OOM;
@@ -370,6 +548,7 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
   n->plan = p;
   n->P = P;
   n->contraction = contraction;
+  n->time_form = time_form ? 1 : 0;
   null_consts& c = n->c;
   c.en = in.eps_num;
   c.ed = in.eps_den;
@@ -418,16 +597,44 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
   sh.d_status = p->d_status;
   share_allocator(&sh, p);
 
+  // The per-interferer L x L products of the time-domain form: the dense FP32 kernel with B := P.
+  if (time_form) {
+    fbst_plan_s& sx = n->shx;
+    sx.info = in;
+    sx.info.B = P;
+    sx.info.N = L;
+    sx.info.L = 2 * L;
+    sx.info.stage2 = FBST_STAGE2_DENSE_FP32;
+    sx.geom = p->geom;
+    sx.band = p->band;
+    sx.device = p->device;
+    sx.d_status = p->d_status;
+    share_allocator(&sx, p);
+  }
+
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int maxb = p->band.max_blocks;
   double* dirs_dev = nullptr;
   double2* xdir = nullptr;
+  double2* rows64 = nullptr;   // F_x (FP64), time-domain form
+  double2* xvt = nullptr;      // Gohberg-Semencul spectra of T = F_x^H F_x
+  double2* xht = nullptr;      // F_x T^{-1} = (F_x^+)^H (FP64)
   int r = FBST_OK;
   do {
     if ((r = plan_alloc_n(p, &n->Q, (size_t)B * L * P * L)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->XV64, (size_t)P * 2 * in.P_gs)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->rhs, (size_t)maxb * P * L)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &n->corr, (size_t)maxb * B * L)) != FBST_OK) break;
+    if (time_form) {
+      if ((r = plan_alloc_n(p, &n->Gx, (size_t)P * 2 * L * L)) != FBST_OK) break;   // FP64
+      if ((r = plan_alloc_n(p, &n->Xrep, (size_t)P * L * 2 * L)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &n->yext, (size_t)maxb * P * 2 * L)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &n->bh, (size_t)maxb * P * L)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &n->tmp, (size_t)maxb * B * in.N)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &rows64, (size_t)2 * L * L)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &xvt, (size_t)2 * in.P_gs)) != FBST_OK) break;
+      if ((r = plan_alloc_n(p, &xht, (size_t)2 * L * L)) != FBST_OK) break;
+    }
     if (!interferers) {
       if ((r = plan_alloc_n(p, &n->ifirst, (size_t)P)) != FBST_OK) break;
       if ((r = plan_alloc_n(p, &n->iwts, iwts.size())) != FBST_OK) break;
@@ -451,7 +658,51 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
                                                                                 p->d_status);
     if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     if ((r = fft64_rows(n->XV64, 2 * P, in.P_gs, p->tw64, -1, s)) != FBST_OK) break;
-    if ((r = build_G(in.P_gs, n->XV64, n->Q, c, B, p->tw64, s)) != FBST_OK) break;
+    if ((r = build_G(in.P_gs, n->XV64, n->Q, c, B, p->tw64, s, !time_form)) != FBST_OK) break;
+    if (time_form) {
+      // F_x (FP64, host) -> Gx = F_x A_{p_j}^{-1} and F_x T^{-1} = (F_x^+)^H, T = F_x^H F_x, both
+      // by the FP64 Gohberg-Semencul apply on the rows of F_x (T's spectra from its Levinson
+      // column, computed on the host); F_x^+ rounded once to complex64.
+      const int Nu = 2 * L, PG = in.P_gs;
+      std::vector<std::complex<double>> F, a, xT;
+      time_rows(in, F);
+      time_gram_row(in, a);
+      if (!levinson_host(a, xT) || !(xT[0].real() > 0.0)) { r = FBST_ERR_NUMERIC; break; }
+      std::vector<std::complex<double>> sp((size_t)2 * PG, {0.0, 0.0});
+      const double sc = 1.0 / (std::sqrt(xT[0].real()) * PG);
+      for (int k = 0; k < L; ++k) {
+        sp[k] = xT[k] * sc;
+        if (k >= 1) sp[PG + k] = std::conj(xT[L - k]) * sc;
+      }
+      if (cudaMemcpy(rows64, F.data(), sizeof(double2) * F.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(xvt, sp.data(), sizeof(double2) * sp.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        r = FBST_ERR_CUDA;
+        break;
+      }
+      if ((r = fft64_rows(xvt, 2, PG, p->tw64, -1, s)) != FBST_OK) break;
+      if ((r = build_G(PG, n->XV64, nullptr, c, B, p->tw64, s, true, rows64, Nu, n->Gx)) != FBST_OK) break;
+      null_consts c1 = c;
+      c1.P = 1;
+      if ((r = build_G(PG, xvt, nullptr, c1, B, p->tw64, s, true, rows64, Nu, xht)) != FBST_OK) break;
+      std::vector<std::complex<double>> xh((size_t)Nu * L);
+      if (cudaMemcpyAsync(xh.data(), xht, sizeof(double2) * xh.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        r = FBST_ERR_CUDA;
+        break;
+      }
+      // F_x^+ [L][Nu] = conj(xh)^T, once per interferer.
+      std::vector<float2> xi((size_t)P * L * Nu);
+      for (int ell = 0; ell < L; ++ell)
+        for (int nn = 0; nn < Nu; ++nn) {
+          const std::complex<double> v = std::conj(xh[(size_t)nn * L + ell]);
+          for (int j = 0; j < P; ++j)
+            xi[((size_t)j * L + ell) * Nu + nn] = make_float2((float)v.real(), (float)v.imag());
+        }
+      if (cudaMemcpy(n->Xrep, xi.data(), sizeof(float2) * xi.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        r = FBST_ERR_CUDA;
+        break;
+      }
+    }
     sh.G = n->Q;
     if (contraction == FBST_NULL_TF32X3) {
       if ((r = build_dense_tc_operand(&sh, s)) != FBST_OK) break;
@@ -473,6 +724,9 @@ static int null_create(fbst_null_t* out, fbst_plan_s* p, const int* interferers,
   cudaStreamSynchronize(s);
   plan_free(p, dirs_dev);
   plan_free(p, xdir);
+  plan_free(p, rows64);
+  plan_free(p, xvt);
+  plan_free(p, xht);
   if (r != FBST_OK) {
     free_null(n);
     delete n;
@@ -497,8 +751,33 @@ int fbst_null_create_directions(fbst_null_t* out, fbst_plan_t p, const double* d
   return null_create(out, p, nullptr, directions, K, P, contraction, stream);
 }
 
+int fbst_null_create_time(fbst_null_t* out, fbst_plan_t p, const int* interferers, int P, int contraction,
+                          void* stream) {
+  if (out) *out = nullptr;
+  if (!interferers) return FBST_ERR_INVALID;
+  return null_create(out, p, interferers, nullptr, 0, P, contraction, stream, true);
+}
+
+int fbst_null_apply_time(fbst_null_t n, const void* y, const void* y_int, void* out, int nblk, void* stream) {
+  if (!n || nblk < 0) return FBST_ERR_INVALID;
+  if (!n->time_form) return FBST_ERR_UNSUPPORTED;
+  if (nblk == 0) return FBST_OK;
+  if (!y || !y_int || !out || !aligned16(y) || !aligned16(y_int) || !aligned16(out)) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fbst_info& in = n->plan->info;
+  const int maxb = n->plan->band.max_blocks;
+  for (int c0 = 0; c0 < nblk; c0 += maxb) {
+    const int nb = std::min(maxb, nblk - c0);
+    const size_t oy = (size_t)c0 * in.B * in.N, oi = (size_t)c0 * n->P * 2 * in.L;
+    FBST_TRY(time_chunk(n, static_cast<const float2*>(y) + oy, static_cast<const float2*>(y_int) + oi,
+                        static_cast<float2*>(out) + oy, nb, s));
+  }
+  return FBST_OK;
+}
+
 int fbst_null_apply(fbst_null_t n, const void* w, void* wt, int nblk, void* stream) {
   if (!n || nblk < 0) return FBST_ERR_INVALID;
+  if (n->time_form) return FBST_ERR_UNSUPPORTED;
   if (nblk == 0) return FBST_OK;
   if (!w || !wt || !aligned16(w) || !aligned16(wt)) return FBST_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -522,10 +801,22 @@ int fbst_null_execute(fbst_null_t n, const void* y, void* bhat, int nblk, void* 
   const int maxb = p->band.max_blocks;
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
+    float2* ob = static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N;
     FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
+    if (n->time_form) {
+      // Eq. (15): the plain beams, the interferers' beams over the broader interval, then the
+      // time-domain subtraction.
+      FBST_TRY(launch_czt_space_scaled(p, p->ws_yhat, p->ws_w, nb, 0, s));
+      FBST_TRY(run_stage2(p, p->ws_w, ob, nb, s, true));
+      k_null_yext64<<<dim3(2 * in.L, n->P, (nb + 7) / 8), 32, 0, s>>>(n->Gx, p->ws_w, n->yext, n->c, in.B, nb,
+                                                                       2 * in.L);
+      FBST_CUDA_TRY(cudaGetLastError());
+      FBST_TRY(time_chunk(n, ob, n->yext, ob, nb, s));
+      continue;
+    }
     FBST_TRY(launch_czt_space(p, p->ws_yhat, p->ws_w, nb, s));
     FBST_TRY(null_chunk(n, p->ws_w, p->ws_w, nb, s));
-    FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s));
+    FBST_TRY(run_stage2(p, p->ws_w, ob, nb, s));
   }
   return FBST_OK;
 }
@@ -534,6 +825,8 @@ int fbst_null_launch_count(fbst_null_t n, int nblk) {
   if (!n || nblk <= 0) return 0;
   const int maxb = n->plan->band.max_blocks;
   const int chunks = (nblk + maxb - 1) / maxb;
+  if (n->time_form)  // stage 1, plain stage 2, F_x A_p^{-1} (FP64), F_x^{-1}, contraction, stage 2, sub
+    return chunks * (2 + stage2_launches(n->plan, true) + 4 + stage2_launches(n->plan, false));
   return chunks * (2 + 3 + stage2_launches(n->plan, false));
 }
 

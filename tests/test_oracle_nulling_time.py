@@ -7,8 +7,10 @@ every matrix literally (pseudo-inverse, dense solve), independently of the Eq. (
 bracket, which is itself pinned against the array-space projection (test_oracle_nulling.py).
 Pins:
 
-* on the broader interval (L samples centred on the block) F_x^+ F_x = I, and Eq. (15) gives the
+* on the broader interval (2L samples centred on the block) F_x^+ F_x = I, and Eq. (15) gives the
   Eq. (14) result for one and two interferers, linear and rectangular arrays;
+* why 2L: an interval of only L samples makes F_x square but ill conditioned as L grows (the
+  stretched frequencies interleave near half a cycle per sample), while 2L keeps it near 1;
 * the defining identity of G': G'_{b,p} F_x beta = F_u H_{b,p} beta for any beta;
 * on the block's own N samples (the Nyquist interval, N < L) F_x is fat, F_x^+ F_x != I, and the
   time-domain form no longer equals Eq. (14): the broader interval is what makes it exact;
@@ -35,7 +37,7 @@ def _problem(kind, mx, my, bx, by, N):
 def test_broader_interval_makes_time_domain_nulling_equal_eq14(kind, mx, my, bx, by, N, ints):
     pb = _problem(kind, mx, my, bx, by, N)
     n0, Nu = O.time_interval(pb)
-    assert Nu == pb.L and n0 == -((pb.L - pb.N) // 2)
+    assert Nu == 2 * pb.L and n0 == -((2 * pb.L - pb.N) // 2)
     Fx = O.F_u_interval(pb, n0, Nu)
     assert np.abs(np.linalg.pinv(Fx) @ Fx - np.eye(pb.L)).max() < 1e-10
     # The block's own samples are rows -n0 .. -n0 + N - 1 of the broader interval.
@@ -80,3 +82,14 @@ def test_no_interferers_is_the_plain_transform():
     w = O.fan_coefficients(pb, y, f.out.beams)
     plain = f.out.apply(w)
     assert np.array_equal(f.apply(plain, np.zeros((1, 0, pb.L))), plain)
+
+
+def test_interval_of_2l_samples_is_well_conditioned():
+    conds = []
+    for N in (64, 256):
+        pb = _problem("ula", 12, 1, 12, 1, N)
+        n0, Nu = O.time_interval(pb)
+        square = O.F_u_interval(pb, -((pb.L - pb.N) // 2), pb.L)
+        conds.append((np.linalg.cond(O.F_u_interval(pb, n0, Nu)), np.linalg.cond(square)))
+    assert all(c2 < 20 for c2, _ in conds)
+    assert conds[1][1] > 1e6          # L = 512 samples only: numerically singular
