@@ -10,7 +10,7 @@ accumulation (FP32-class: its error against the FP64 oracle is measured and repo
 CUDA-core apply. One step = fbst_execute over the 64 blocks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fbst|reference] [--stage2 VARIANT]
-                  [--workload ULA1024|NU1024|C2|C3|C4|C5|C2N|C2NT|OG|STREAM] [--contraction tf32x3|fp32]
+                  [--workload ULA1024|NU1024|C2|C3|NUC3|C4|C5|C2N|C2NT|OG|STREAM|GEN] [--contraction tf32x3|fp32]
 
 With N > 1 (torchrun) every rank runs its own replica of the plan on its own share of the
 stream's blocks (rank r takes blocks [r*nblk, (r+1)*nblk) of one continuous record: weak scaling;
@@ -103,14 +103,19 @@ def path_bytes(info, nblk: int) -> float:
     return 8.0 * nblk * (M * N + B * N + B * L)
 
 
-def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str, fp32: dict) -> dict:
+def roofline(kernel: str, info, nblk: int, ms: float, peaks: dict, peak_kind: str, fp32: dict,
+             w_scales_from_stage1: bool = False) -> dict:
     """Roofline entry of one kernel launch (nblk blocks) that took `ms` milliseconds. `fp32` is the
-    FP32 ALU peak ({"tflops", "source"}), measured where possible."""
+    FP32 ALU peak ({"tflops", "source"}), measured where possible. w_scales_from_stage1: the FP16
+    split's per-block scales of w come from the spatial chirp-z (inside fbst_execute on a linear
+    grid array), so stage 2 reads w once instead of twice."""
     fp32_peak = float(fp32["tflops"])
     flops = flop_model(info)[kernel] * nblk
     M, N, B, L = info.M, info.N, info.B, info.L
     if kernel == "stage2" and info.stage2 in TC_VARIANTS:
         npl, esz, terms, dt, wpass = TC_VARIANTS[info.stage2]
+        if w_scales_from_stage1 and dt == "f16":
+            wpass = 1
         nbytes = float(B) * npl * N * L * esz + wpass * B * L * nblk * 8.0 + B * N * nblk * 8.0
         hbm = float(peaks["hbm_gbs"])
         tc_peak, tc_src = tc_peak_of(peaks, dt)
@@ -222,10 +227,11 @@ def workload(args, first_block: int = 0):
         return dict(kind="ula", mx=c["mx"], my=1, bx=c["bx"], by=1, N=c["N"], frac_bw=c["frac_bw"], nblk=nb,
                     name=args.workload, offsets=configs.config_geometry(args.workload).offsets), \
             lambda: configs.config_data(args.workload, nblk=nb, first_block=first_block)["y"]
-    if args.workload == "C3":
-        nb = args.nblk or configs.CONFIGS["C3"]["nblk"]
-        return dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, nblk=nb, name="C3"), \
-            lambda: configs.config_data("C3", nblk=nb, Q=64)["y"]
+    if args.workload in ("C3", "NUC3"):
+        nb = args.nblk or configs.CONFIGS[args.workload]["nblk"]
+        return dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, nblk=nb, name=args.workload,
+                    offsets=configs.config_geometry(args.workload).offsets), \
+            lambda: configs.config_data(args.workload, nblk=nb, Q=64)["y"]
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -579,6 +585,73 @@ def run_null(args) -> None:
     if cpu is not None:
         line["cpu_baseline"] = cpu
     nl.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_gen(args) -> None:
+    """GEN: the solve for the stage-2 generators x_b = A_b^{-1} e_0 (Sec. V) of every beam of a
+    1024-element ULA plan (1024 Hermitian positive definite Toeplitz systems, L = 2N), in FP64 on
+    the GPU: the superfast solver (doubling Schur algorithm with FFT polynomial products,
+    O(L log^2 L)) against the Levinson recursion (O(L^2)). One step = fbst_solve_generators (the
+    generators a_b in FP64 and the solve). --gen-n sets N (512: L = 1024, the ULA1024 plan;
+    1024: L = 2048, the largest L)."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--workload GEN runs on one GPU")
+    import torch
+    import paper_2512_08887_gb300 as fb
+    from paper_2512_08887_gb300.build import build
+    import oracle as O
+    build()
+    torch.cuda.set_device(0)
+    M, N = 1024, args.gen_n
+    plan = fb.Plan(fb.make_geometry("ula", M), N, fb.make_band(0.5, stage2="gs", max_blocks=1))
+    B, L = plan.B, plan.L
+    x = {m: torch.empty((B, L), dtype=torch.complex128, device="cuda") for m in ("superfast", "levinson")}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(method):
+        for _ in range(args.warmup):
+            plan.solve_generators(method, x[method])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            plan.solve_generators(method, x[method])
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    t_sf = timed("superfast")
+    clocks = sampler.stop()
+    t_lev = timed("levinson")
+    if plan.sync_status() != 0:
+        raise SystemExit("a generator solve reported an error")
+    xs, xl = x["superfast"].cpu().numpy(), x["levinson"].cpu().numpy()
+    i = plan.info
+    pb = O.make_problem("ula", M, 1, M, 1, N, frac_bw=i.fb_num / i.fb_den, epsilon=i.eps_num / i.eps_den,
+                        delta=i.delta, L=L)
+    beams = [0, B // 2 + 1]
+    errs = {"superfast": 0.0, "levinson": 0.0}
+    for b in beams:
+        ref = np.linalg.solve(O.gram(pb, b), np.eye(L)[:, 0])
+        for m, xv in (("superfast", xs), ("levinson", xl)):
+            errs[m] = max(errs[m], O.rel_l2(xv[b], ref))
+    ms = statistics.mean(t_sf)
+    line = {"metric": "Toeplitz generator systems solved/s (FP64, rel err vs dense solve)", "value": B / (ms / 1e3),
+            "unit": "systems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"GEN: generators of the ULA M={M} B={B} N={N} L={L} plan, {B} systems per step, "
+                                   "superfast (doubling Schur) vs Levinson",
+                       "l2": "flushed before every timed step (256 MiB write, untimed)"},
+            "levinson_value": B / (statistics.mean(t_lev) / 1e3), "levinson_ms_per_step": statistics.mean(t_lev),
+            "speedup_vs_levinson": statistics.mean(t_lev) / ms,
+            "rel_err_vs_dense_solve": errs, "superfast_vs_levinson": O.rel_l2(xs, xl),
+            "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "roofline": None, "roofline_note": "FP64 latency-bound recursion (sequential Schur steps and FFT passes "
+                                               "per system); no measured FP64 peak to set a roof"}
     print(json.dumps(line), flush=True)
 
 
@@ -963,6 +1036,7 @@ def main() -> None:
     ap.add_argument("--mem-budget", type=int, default=8 << 30)
     ap.add_argument("--batch-work", type=float, default=4e6)
     ap.add_argument("--hop", type=int, default=384)
+    ap.add_argument("--gen-n", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -983,6 +1057,9 @@ def main() -> None:
         return
     if args.workload == "STREAM":
         run_stream(args)
+        return
+    if args.workload == "GEN":
+        run_gen(args)
         return
 
     import torch
@@ -1052,6 +1129,9 @@ def main() -> None:
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
+    # The library's stage trace: events on the launching stream around each stage of every timed
+    # fbst_execute call, so the kernel times are those of the timed steps themselves.
+    plan.trace_stages(args.steps)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -1070,8 +1150,13 @@ def main() -> None:
     total_ms = max_over_ranks(sum(step_ms))
     units = float(nblk) * B * N * world
     value = whole_job_rate(float(nblk) * B * N * args.steps, world, total_ms / 1e3)
+    trace = plan.trace_read(args.steps)
+    plan.trace_stages(0)
+    names = ["czt_time", "czt_space", "stage2"]
+    kern_ms = {n: statistics.mean(t[j] for t in trace) for j, n in enumerate(names)}
 
-    # Per-kernel live timing: each kernel through its own C-ABI stage call, events on its stream.
+    # The same kernels through their own C-ABI stage calls (stage 2 of the FP16 split then runs
+    # its own pass for the scales of w): reported beside the in-step times.
     kin = min(args.steps, 200)
     yhat = torch.empty((nblk, info.L, M), dtype=torch.complex64, device=dev)
     wbuf = torch.empty((nblk, B, info.L), dtype=torch.complex64, device=dev)
@@ -1086,8 +1171,8 @@ def main() -> None:
         plan.toeplitz_apply(wbuf, out, nblk)
         ev[i][3].record(stream)
     torch.cuda.synchronize()
-    names = ["czt_time", "czt_space", "stage2"]
-    kern_ms = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin)) for j, n in enumerate(names)}
+    kern_ms_calls = {n: statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(kin))
+                     for j, n in enumerate(names)}
 
     # End to end through the host-buffer entry point, pinned host memory, copies included.
     e2e_steps = min(args.steps, 200)
@@ -1111,7 +1196,10 @@ def main() -> None:
     peaks, peak_kind = load_peaks()
     fp32 = measure_fp32_peak(fb, torch.cuda.current_device())
     dom = max(kern_ms, key=kern_ms.get)
-    roof = roofline(dom, info, nblk, kern_ms[dom], peaks, peak_kind, fp32)
+    # Inside fbst_execute the spatial chirp-z of a linear grid array supplies the FP16 split's
+    # scales of w; the stand-alone stage-2 call makes its own pass for them.
+    scales_in_step = w["kind"] == "ula" and w.get("offsets") is None
+    roof = roofline(dom, info, nblk, kern_ms[dom], peaks, peak_kind, fp32, scales_in_step)
     s2name = fb.STAGE2_NAMES[info.stage2]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -1158,7 +1246,11 @@ def main() -> None:
         "path_roofline": path_roofline(info, nblk, statistics.mean(step_ms), peaks, fp32),
         "roofline": dict(roof, kernel=dom, traffic=traffic),
         "kernels_ms": kern_ms,
-        "kernels_roofline": {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32) for k, v in kern_ms.items()},
+        "kernels_timing": "device time of each stage inside the timed fbst_execute steps (the library's stage "
+                          "trace: CUDA events on the launching stream between the stages)",
+        "kernels_roofline": {k: roofline(k, info, nblk, v, peaks, peak_kind, fp32, scales_in_step)
+                             for k, v in kern_ms.items()},
+        "kernels_ms_separate_calls": kern_ms_calls,
         "fp32_peak": fp32,
         "e2e": {"value": units * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": int(8 * nblk * M * N), "d2h_bytes_per_step": int(8 * nblk * B * N)},

@@ -69,6 +69,14 @@ enum fbst_stage2_kind {
                                   at twice the TF32 MMA rate */
 };
 
+/* How the plan solves for the stage-2 generators x_b = A_b^{-1} e_0 (Sec. V), in FP64. Both give
+ * the same x up to rounding (both are tested against a dense solve). */
+enum fbst_generator_solver {
+  FBST_GEN_LEVINSON = 0,  /* Levinson recursion, O(L^2) per beam, one CTA per beam */
+  FBST_GEN_SUPERFAST = 1  /* doubling Schur algorithm with FFT polynomial products, O(L log^2 L)
+                             per beam (the fast generator computation Sec. V points to); L <= 2049 */
+};
+
 /* Array and beam grid. M = mx*my elements, B = bx*by beams. A linear array has my = by = 1. */
 typedef struct {
   int kind;   /* FBST_ULA or FBST_URA */
@@ -87,6 +95,7 @@ typedef struct {
   int delta_relative; /* nonzero: the plan uses delta*M*N (M*N is the diagonal of F_b^H F_b) */
   int stage2;         /* enum fbst_stage2_kind */
   int max_blocks;     /* blocks the plan's workspace holds; larger nblk run in chunks (>= 1) */
+  int generator_solver; /* enum fbst_generator_solver (0: Levinson) */
 } fbst_band;
 
 /* Everything the plan derived from its arguments. */
@@ -143,17 +152,22 @@ typedef void (*fbst_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, const fbst_band* band,
               void* stream, fbst_alloc_fn alloc, fbst_free_fn free, void* ctx);
 
-/* fbst_plan for a linear array whose elements sit at arbitrary positions (Sec. IX, Eq. (16)):
- * positions (host, [M][2] doubles, (x, 0) in half wavelengths at f_c + Omega, element m's delay
- * rho*u*x_m; NULL gives the grid, i.e. fbst_plan). Off the grid only the element sum of stage 1b
- * changes: it becomes a type-1 non-uniform FFT per frequency (each element spread onto an
- * oversampled grid of nf = pow2(>= 2B) points with a 9-point "exponential of semicircle" kernel,
- * an nf-point FFT, division by the kernel's Fourier transform; kernel error about 1e-8, below the
- * FP32 rounding), and the Toeplitz generators of A_b are direct FP64 sums over the positions.
- * Stage 1a, the Levinson solves and every stage-2 variant are those of fbst_plan. info.P_space_x
- * reports nf. Rectangular arrays off the grid are FBST_ERR_UNSUPPORTED (their element sum would be
- * a two-dimensional transform), and so are nulling and off-grid objects on such a plan; batches
- * accept it. A position that is not finite, or a nonzero y, is FBST_ERR_INVALID. */
+/* fbst_plan for an array whose elements sit at arbitrary positions (Sec. IX, Eq. (16)):
+ * positions (host, [M][2] doubles, (x, y) in half wavelengths at f_c + Omega, element m's delay
+ * rho*(u*x_m + v*y_m); y = 0 for a linear array; NULL gives the grid, i.e. fbst_plan; element m is
+ * the m-th element of y's [M] axis). Off the grid only the element sum of stage 1b changes: it
+ * becomes a type-1 non-uniform FFT per frequency: for a linear array each element is spread onto
+ * an oversampled grid of nf = pow2(>= 2B) points with a 9-point "exponential of semicircle"
+ * kernel, then an nf-point FFT and division by the kernel's Fourier transform; for a rectangular
+ * array onto an nf_x x nf_y grid (pow2 >= 2 bx, 2 by) with the 9 x 9 product kernel, then a 2-D
+ * FFT and the two axes' factors (kernel error about 1e-8 per axis, below the FP32 rounding). The
+ * Toeplitz generators of A_b are direct FP64 sums over the positions. Stage 1a, the generator
+ * solves and every stage-2 variant are those of fbst_plan. info.P_space_x (and P_space_y) report
+ * the grid sizes. A rectangular array whose grid exceeds 128 x 128 points, or whose kernel would
+ * need more than the 227 KB of shared memory (the grid, its FFT buffers and a [B][5] output tile),
+ * is FBST_ERR_UNSUPPORTED, and so are nulling and off-grid objects on any such plan; batches
+ * accept a linear one. A position that is not finite, or a nonzero y on a linear array, is
+ * FBST_ERR_INVALID. */
 int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* positions, int M, int N, int B,
                         const fbst_band* band, void* stream, fbst_alloc_fn alloc, fbst_free_fn free, void* ctx);
 
@@ -229,6 +243,23 @@ int fbst_set_wait_limit(fbst_plan_t p, uint64_t ns);
  * NULL) the timed launch's duration (CUDA events on `stream`, which the call synchronises). */
 int fbst_fp32_fma_peak(void* sink, int iters, double* tflops, double* ms, void* stream);
 
+/* Tracing; no counterpart in the paper. From now on record CUDA events (timing enabled) on the
+ * call's stream around the three stages of every fbst_execute call: before stage 1a, between 1a
+ * and 1b, between 1b and stage 2, after stage 2 (of the call's first chunk when nblk exceeds
+ * max_blocks), for the last `capacity` calls (a ring). capacity 0 stops tracing and frees the
+ * events; a new capacity drops what was recorded. The events cost four cudaEventRecord calls per
+ * traced call and no kernel. Host-side state: calls on one plan from several host threads at once
+ * are not supported while tracing. FBST_ERR_INVALID (NULL plan, capacity < 0 or > 2^20),
+ * FBST_ERR_OOM, FBST_ERR_CUDA (event creation). */
+int fbst_trace_stages(fbst_plan_t p, int capacity);
+
+/* Wait for the traced calls not read yet and write the device time, in milliseconds, of their
+ * stage 1a, stage 1b and stage 2 to ms[3*i], ms[3*i + 1], ms[3*i + 2], oldest call first, for at
+ * most max_calls calls (ms holds 3*max_calls floats, host memory). Returns the number of calls
+ * written (>= 0; the others are dropped) or a negative status: FBST_ERR_INVALID (NULL plan, or ms
+ * NULL with max_calls > 0), FBST_ERR_CUDA. */
+int fbst_trace_read(fbst_plan_t p, float* ms, int max_calls);
+
 /* Error reporting; no counterpart in the paper. Synchronise `stream`, then return and clear the
  * plan's device status word: FBST_OK, or the
  * error a kernel recorded since the last check (FBST_ERR_TIMEOUT when a bounded device-side wait
@@ -239,9 +270,21 @@ int fbst_sync_status(fbst_plan_t p, void* stream);
  * caller's *out. FBST_ERR_INVALID if p or out is NULL. */
 int fbst_plan_info(fbst_plan_t p, fbst_info* out);
 
-/* Copy the first column x_b of A_b^{-1} for every beam (FP64 Levinson result, Sec. V) to host
- * memory `x_host` as [B][L] complex128 (interleaved doubles). Exposed for testing. */
+/* Copy the first column x_b of A_b^{-1} for every beam (the FP64 result of the plan's generator
+ * solver, Sec. V) to host memory `x_host` as [B][L] complex128 (interleaved doubles). Exposed for
+ * testing. */
 int fbst_plan_generators(fbst_plan_t p, void* x_host);
+
+/* Solve again for the generators of Sec. V, x_b = A_b^{-1} e_0 for every beam b of the plan, with
+ * the given enum fbst_generator_solver, from the plan's Toeplitz generators a_b (recomputed in
+ * FP64, as at plan time). x: device memory, [B][L] complex128 (interleaved doubles), written by
+ * the call; the plan's own generators are not changed. Enqueued on `stream` (NULL: the legacy
+ * default stream) with a stream-ordered temporary of the plan's allocator (the superfast solver's
+ * workspace: one slot of about 18 L complex128 per resident CTA). Errors: FBST_ERR_INVALID (NULL
+ * plan or x, unknown method), FBST_ERR_UNSUPPORTED (superfast with L > 2049), FBST_ERR_OOM; a
+ * pivot that is not positive records FBST_ERR_NUMERIC for fbst_sync_status. For testing and for
+ * timing the two solvers. */
+int fbst_solve_generators(fbst_plan_t p, int method, void* x, void* stream);
 
 /* Resource management; no counterpart in the paper. Free the plan and all of its device memory
  * (including that of nulling objects still built on it) through its free function, in stream order

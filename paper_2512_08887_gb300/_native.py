@@ -20,6 +20,7 @@ ULA, URA = 0, 1
 STAGE2 = {"auto": 0, "gs": 1, "gs_ir1": 2, "dense_fp32": 3, "dense_bf16x3": 4, "dense_tf32": 5,
           "dense_tf32x3": 6, "dense_f16x3": 7}
 STAGE2_NAMES = {v: k for k, v in STAGE2.items()}
+GENERATOR_SOLVER = {"levinson": 0, "superfast": 1}
 
 
 class FBSTError(RuntimeError):
@@ -38,7 +39,7 @@ class Geometry(C.Structure):
 class Band(C.Structure):
     _fields_ = [("frac_bw", C.c_double), ("epsilon", C.c_double), ("gamma_num", C.c_int),
                 ("gamma_den", C.c_int), ("delta", C.c_double), ("delta_relative", C.c_int),
-                ("stage2", C.c_int), ("max_blocks", C.c_int)]
+                ("stage2", C.c_int), ("max_blocks", C.c_int), ("generator_solver", C.c_int)]
 
 
 class Info(C.Structure):
@@ -72,6 +73,9 @@ SIGNATURES = {
     "fbst_plan_info": (_I, [_VP, C.POINTER(Info)]),
     "fbst_sync_status": (_I, [_VP, _VP]),
     "fbst_plan_generators": (_I, [_VP, _VP]),
+    "fbst_solve_generators": (_I, [_VP, _I, _VP, _VP]),
+    "fbst_trace_stages": (_I, [_VP, _I]),
+    "fbst_trace_read": (_I, [_VP, C.POINTER(C.c_float), _I]),
     "fbst_destroy": (_I, [_VP]),
     "fbst_status_string": (C.c_char_p, [_I]),
     "fbst_last_error": (C.c_char_p, []),
@@ -157,9 +161,10 @@ def make_geometry(kind: str, mx: int, my: int = 1, bx: int | None = None, by: in
 
 
 def make_band(frac_bw: float, epsilon: float = 1.01, gamma=(2, 1), delta: float = 1e-3,
-              delta_relative: bool = True, stage2: str = "auto", max_blocks: int = 64) -> Band:
+              delta_relative: bool = True, stage2: str = "auto", max_blocks: int = 64,
+              generator_solver: str = "levinson") -> Band:
     return Band(float(frac_bw), float(epsilon), int(gamma[0]), int(gamma[1]), float(delta),
-                int(bool(delta_relative)), STAGE2[stage2], int(max_blocks))
+                int(bool(delta_relative)), STAGE2[stage2], int(max_blocks), GENERATOR_SOLVER[generator_solver])
 
 
 def derive(geom: Geometry, N: int, band: Band) -> Info:
@@ -237,7 +242,8 @@ class Plan:
     `allocator`: "torch" (default) takes the plan's device memory from PyTorch's caching
     allocator; None lets the library use cudaMallocAsync; or an Allocator. Its memory is allocated
     and freed in stream order on `stream` (default: the current stream), which must outlive the plan.
-    `positions` (M (x, y) pairs, half wavelengths): a linear array off the grid (Sec. IX).
+    `positions` (M (x, y) pairs, half wavelengths): a linear or rectangular array off the grid
+    (Sec. IX).
     """
 
     def __init__(self, geom: Geometry, N: int, band: Band, stream=None, allocator="torch", positions=None):
@@ -335,11 +341,33 @@ class Plan:
         return tuple(out)
 
     def generators(self):
-        """First column of every A_b^{-1} from the FP64 Levinson solve, numpy complex128 [B][L]."""
+        """First column of every A_b^{-1} from the plan's FP64 solve, numpy complex128 [B][L]."""
         import numpy as np
         out = np.empty((self.B, self.L), dtype=np.complex128)
         _check(self._lib.fbst_plan_generators(self._h, out.ctypes.data), "fbst_plan_generators")
         return out
+
+    def trace_stages(self, capacity: int) -> None:
+        """Record stage times of the next `capacity` execute calls (0 stops tracing)."""
+        _check(self._lib.fbst_trace_stages(self._h, int(capacity)), "fbst_trace_stages")
+
+    def trace_read(self, max_calls: int):
+        """Per traced execute call, oldest first: (stage 1a, stage 1b, stage 2) device ms."""
+        buf = (C.c_float * (3 * max(1, int(max_calls))))()
+        n = self._lib.fbst_trace_read(self._h, buf, int(max_calls))
+        if n < 0:
+            _check(n, "fbst_trace_read")
+        return [tuple(buf[3 * i:3 * i + 3]) for i in range(n)]
+
+    def solve_generators(self, method: str, x, stream=None) -> None:
+        """Solve again for every x_b = A_b^{-1} e_0 with `method` ("levinson" or "superfast") into
+        x, a complex128 CUDA tensor [B][L], on `stream` (default: torch's current stream)."""
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex128
+                and x.is_contiguous() and x.numel() == self.B * self.L):
+            raise ValueError("x must be a contiguous complex128 CUDA tensor of B*L elements")
+        _check(self._lib.fbst_solve_generators(self._h, GENERATOR_SOLVER[method], _ptr(x), _stream(stream)),
+               "fbst_solve_generators")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "launch_util.cuh"
 
 namespace fbst {
 
@@ -135,21 +136,41 @@ int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* 
   if ((alloc == nullptr) != (free_fn == nullptr)) return FBST_ERR_INVALID;
   fbst_info info;
   FBST_TRY(fbst_derive(g, M, N, B, band, &info));
-  if (g->kind == FBST_URA && info.P_space_x != info.P_space_y) return FBST_ERR_UNSUPPORTED;
-  // A non-uniform linear array: stage 1b becomes a type-1 NUFFT onto an oversampled grid of
-  // nf >= 2B points (its size replaces the chirp-z size in info.P_space_x).
-  int nu_nf = 0;
+  if (g->kind == FBST_URA && !positions && info.P_space_x != info.P_space_y) return FBST_ERR_UNSUPPORTED;
+  // Elements off the grid: stage 1b becomes a type-1 NUFFT onto an oversampled grid of nf >= 2B
+  // points (a linear array), or of nf_x x nf_y >= 2 bx x 2 by points (a rectangular array); the
+  // grid sizes replace the chirp-z sizes in info.P_space_x / P_space_y.
+  int nu_nf = 0, nu_nfy = 0;
   const int nu_w = 9;
   if (positions) {
-    if (g->kind != FBST_ULA) return FBST_ERR_UNSUPPORTED;
     for (int m = 0; m < M; ++m)
-      if (!std::isfinite(positions[2 * m]) || positions[2 * m + 1] != 0.0) return FBST_ERR_INVALID;
-    nu_nf = 16;
-    while (nu_nf < 2 * B) nu_nf <<= 1;
-    if (nu_nf > kMaxFFT) return FBST_ERR_UNSUPPORTED;
+      if (!std::isfinite(positions[2 * m]) || !std::isfinite(positions[2 * m + 1])) return FBST_ERR_INVALID;
     const size_t c64 = sizeof(float2), L = info.L;
     info.table_bytes -= c64 * L * ((size_t)g->mx + info.P_space_x + g->bx);
-    info.table_bytes += sizeof(double) * M + (sizeof(int) + sizeof(float)) * L * M + sizeof(float) * B;
+    if (g->kind == FBST_ULA) {
+      for (int m = 0; m < M; ++m)
+        if (positions[2 * m + 1] != 0.0) return FBST_ERR_INVALID;
+      nu_nf = 16;
+      while (nu_nf < 2 * B) nu_nf <<= 1;
+      if (nu_nf > kMaxFFT) return FBST_ERR_UNSUPPORTED;
+      info.table_bytes += sizeof(double) * M + (sizeof(int) + sizeof(float)) * L * M + sizeof(float) * B;
+    } else {
+      nu_nf = 16;
+      while (nu_nf < 2 * g->bx) nu_nf <<= 1;
+      nu_nfy = 16;
+      while (nu_nfy < 2 * g->by) nu_nfy <<= 1;
+      // The 2-D kernel's shared memory: the padded grid, the FFT exchange buffers, the [B][4 + 1]
+      // output tile; grids up to 128 x 128.
+      auto groups_x_nf = [](int nf) { return (size_t)256 / (nf / 2 < 32 ? nf / 2 : 32) * nf; };
+      const size_t smem = sizeof(float) * 2 * nu_nf * ((size_t)nu_nfy + 1) +
+                          c64 * (std::max(groups_x_nf(nu_nf), groups_x_nf(nu_nfy)) + (size_t)B * 5);
+      if (nu_nf > 128 || nu_nfy > 128 || smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
+      if (!(g->mx == g->my && g->bx == g->by))
+        info.table_bytes -= c64 * L * ((size_t)g->my + info.P_space_y + g->by);
+      info.table_bytes += 2 * (sizeof(double) * M + (sizeof(int) + sizeof(float)) * L * M) +
+                          sizeof(float) * ((size_t)g->bx + g->by);
+      info.P_space_y = nu_nfy;
+    }
     info.P_space_x = nu_nf;
   }
   fbst_plan_s* p = new (std::nothrow) fbst_plan_s();
@@ -169,6 +190,7 @@ int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* 
   p->alloc_ctx = ctx;
   p->mem_stream = s;
   p->nu_nf = nu_nf;
+  p->nu_nfy = nu_nfy;
   p->nu_w = nu_nf ? nu_w : 0;
   int r = FBST_OK;
   do {
@@ -193,11 +215,21 @@ int fbst_plan_positions(fbst_plan_t* out, const fbst_geometry* g, const double* 
       if ((r = dmalloc(p, &p->pos, (size_t)M)) != FBST_OK) break;
       if ((r = dmalloc(p, &p->nu_j0, (size_t)L * M)) != FBST_OK) break;
       if ((r = dmalloc(p, &p->nu_dg, (size_t)L * M)) != FBST_OK) break;
-      if ((r = dmalloc(p, &p->nu_deconv, (size_t)B)) != FBST_OK) break;
-      std::vector<double> px(M);
-      for (int m = 0; m < M; ++m) px[m] = positions[2 * m];
+      if ((r = dmalloc(p, &p->nu_deconv, (size_t)(nu_nfy ? g->bx : B))) != FBST_OK) break;
+      if (nu_nfy) {
+        if ((r = dmalloc(p, &p->pos_y, (size_t)M)) != FBST_OK) break;
+        if ((r = dmalloc(p, &p->nu_j0y, (size_t)L * M)) != FBST_OK) break;
+        if ((r = dmalloc(p, &p->nu_dgy, (size_t)L * M)) != FBST_OK) break;
+        if ((r = dmalloc(p, &p->nu_deconv_y, (size_t)g->by)) != FBST_OK) break;
+      }
+      std::vector<double> px(M), py(M);
+      for (int m = 0; m < M; ++m) {
+        px[m] = positions[2 * m];
+        py[m] = positions[2 * m + 1];
+      }
       if (cudaStreamSynchronize(s) != cudaSuccess ||
-          cudaMemcpy(p->pos, px.data(), sizeof(double) * M, cudaMemcpyHostToDevice) != cudaSuccess) {
+          cudaMemcpy(p->pos, px.data(), sizeof(double) * M, cudaMemcpyHostToDevice) != cudaSuccess ||
+          (nu_nfy && cudaMemcpy(p->pos_y, py.data(), sizeof(double) * M, cudaMemcpyHostToDevice) != cudaSuccess)) {
         r = FBST_ERR_CUDA;
         break;
       }
@@ -247,6 +279,8 @@ int fbst_plan(fbst_plan_t* out, const fbst_geometry* g, int M, int N, int B, con
   return fbst_plan_positions(out, g, nullptr, M, N, B, band, stream, alloc, free_fn, ctx);
 }
 
+static void free_trace(fbst_plan_s* p);
+
 int fbst_destroy(fbst_plan_t p) {
   if (!p) return FBST_OK;
   // The host path's copy streams hold no pending work: fbst_execute_host synchronises before it
@@ -255,6 +289,7 @@ int fbst_destroy(fbst_plan_t p) {
     if (c) cudaStreamDestroy(c);
   for (cudaEvent_t e : p->pipe_ev)
     if (e) cudaEventDestroy(e);
+  free_trace(p);
   free_plan_memory(p);
   delete p->mem;
   delete p;
@@ -287,6 +322,21 @@ int fbst_plan_generators(fbst_plan_t p, void* x_host) {
   if (!p || !x_host) return FBST_ERR_INVALID;
   FBST_CUDA_TRY(cudaMemcpy(x_host, p->x64, sizeof(double2) * (size_t)p->info.B * p->info.L, cudaMemcpyDeviceToHost));
   return FBST_OK;
+}
+
+int fbst_solve_generators(fbst_plan_t p, int method, void* x, void* stream) {
+  if (!p || !x) return FBST_ERR_INVALID;
+  if (method != FBST_GEN_LEVINSON && method != FBST_GEN_SUPERFAST) return FBST_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double2* gen = nullptr;
+  FBST_TRY(plan_alloc_n(p, &gen, (size_t)p->info.B * p->info.L));
+  const bool other = s != p->mem_stream;  // allocated in stream order on the plan's stream
+  int r = (other && cudaStreamSynchronize(p->mem_stream) != cudaSuccess) ? FBST_ERR_CUDA : FBST_OK;
+  if (r == FBST_OK) r = plan_toeplitz_generators(p, gen, s);
+  if (r == FBST_OK) r = solve_generators(p, gen, static_cast<double2*>(x), p->info.B, method, s);
+  if (other) cudaStreamSynchronize(s);
+  plan_free(p, gen);
+  return r;
 }
 
 int fbst_czt_time(fbst_plan_t p, const void* y, void* yhat, int nblk, void* stream) {
@@ -344,13 +394,65 @@ int fbst_execute(fbst_plan_t p, const void* y, void* bhat, int nblk, void* strea
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const fbst_info& in = p->info;
   const int maxb = p->band.max_blocks;
+  // Traced call: events around the three stages of its first chunk.
+  cudaEvent_t* tev = nullptr;
+  if (p->trace_cap > 0 && nblk > 0) {
+    tev = p->trace_ev + 4 * (size_t)(p->trace_next % p->trace_cap);
+    ++p->trace_next;
+    p->trace_count = std::min(p->trace_count + 1, p->trace_cap);
+  }
   for (int c0 = 0; c0 < nblk; c0 += maxb) {
     const int nb = std::min(maxb, nblk - c0);
+    cudaEvent_t* ev = c0 == 0 ? tev : nullptr;
+    if (ev) FBST_CUDA_TRY(cudaEventRecord(ev[0], s));
     FBST_TRY(launch_czt_time(p, static_cast<const float2*>(y) + (size_t)c0 * in.M * in.N, p->ws_yhat, nb, s));
+    if (ev) FBST_CUDA_TRY(cudaEventRecord(ev[1], s));
     FBST_TRY(launch_czt_space_scaled(p, p->ws_yhat, p->ws_w, nb, 0, s));
+    if (ev) FBST_CUDA_TRY(cudaEventRecord(ev[2], s));
     FBST_TRY(run_stage2(p, p->ws_w, static_cast<float2*>(bhat) + (size_t)c0 * in.B * in.N, nb, s, true));
+    if (ev) FBST_CUDA_TRY(cudaEventRecord(ev[3], s));
   }
   return FBST_OK;
+}
+
+static void free_trace(fbst_plan_s* p) {
+  for (int i = 0; i < 4 * p->trace_cap; ++i)
+    if (p->trace_ev[i]) cudaEventDestroy(p->trace_ev[i]);
+  delete[] p->trace_ev;
+  p->trace_ev = nullptr;
+  p->trace_cap = p->trace_next = p->trace_count = 0;
+}
+
+int fbst_trace_stages(fbst_plan_t p, int capacity) {
+  if (!p || capacity < 0 || capacity > (1 << 20)) return FBST_ERR_INVALID;
+  free_trace(p);
+  if (capacity == 0) return FBST_OK;
+  p->trace_ev = new (std::nothrow) cudaEvent_t[4 * (size_t)capacity]();
+  if (!p->trace_ev) return FBST_ERR_OOM;
+  p->trace_cap = capacity;
+  for (int i = 0; i < 4 * capacity; ++i) {
+    const cudaError_t e = cudaEventCreate(&p->trace_ev[i]);
+    if (e != cudaSuccess) {
+      p->trace_ev[i] = nullptr;
+      free_trace(p);
+      set_last_cuda_error(e, "cudaEventCreate", __FILE__, __LINE__);
+      return FBST_ERR_CUDA;
+    }
+  }
+  return FBST_OK;
+}
+
+int fbst_trace_read(fbst_plan_t p, float* ms, int max_calls) {
+  if (!p || (!ms && max_calls > 0) || max_calls < 0) return FBST_ERR_INVALID;
+  const int n = std::min(p->trace_count, max_calls);
+  const int first = p->trace_next - p->trace_count;  // the oldest call not yet read
+  for (int i = 0; i < n; ++i) {
+    cudaEvent_t* ev = p->trace_ev + 4 * (size_t)((first + i) % p->trace_cap);
+    FBST_CUDA_TRY(cudaEventSynchronize(ev[3]));
+    for (int j = 0; j < 3; ++j) FBST_CUDA_TRY(cudaEventElapsedTime(&ms[3 * i + j], ev[j], ev[j + 1]));
+  }
+  p->trace_count = 0;
+  return n;
 }
 
 }  // extern "C"

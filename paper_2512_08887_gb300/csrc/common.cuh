@@ -139,7 +139,14 @@ struct fbst_plan_s {
   double* pos;         // [M] element positions along x, half wavelengths
   int* nu_j0;          // [L][M] first grid point each element reaches
   float* nu_dg;        // [L][M] its grid coordinate minus that point, in (nu_w/2 - 1, nu_w/2]
-  float* nu_deconv;    // [B] 1 / kernel Fourier transform at the beam's mode (and / nu_nf scale)
+  float* nu_deconv;    // [bx] 1 / kernel Fourier transform at the beam's mode (and / nu_nf scale)
+  // A rectangular array off the grid: the y axis of the two-dimensional NUFFT (nu_nfy = 0 for a
+  // linear array); nu_j0 / nu_dg / nu_deconv above then hold the x axis.
+  int nu_nfy;          // oversampled grid size along y (power of two >= 2 by), = info.P_space_y
+  double* pos_y;       // [M] element positions along y, half wavelengths
+  int* nu_j0y;         // [L][M]
+  float* nu_dgy;       // [L][M]
+  float* nu_deconv_y;  // [by]
 
   // Stage 1b: spatial chirp-z per frequency; axis 0 = x (all arrays), axis 1 = y (rectangular).
   fbst_axis_tables ax[2];
@@ -185,6 +192,11 @@ struct fbst_plan_s {
   // Limit of one pipeline wait of the tensor-core stage-2 kernels, ns (0 = the default, 1 s);
   // a wait that runs out makes the kernel record FBST_ERR_TIMEOUT, drain its copies and return.
   unsigned long long wait_ns;
+
+  // Stage trace (fbst_trace_stages): 4 timing events per traced fbst_execute call in a ring of
+  // trace_cap calls; trace_next counts the calls traced, trace_count those not yet read.
+  cudaEvent_t* trace_ev;
+  int trace_cap, trace_next, trace_count;
 
   // Launch shapes of the temporal and spatial chirp-z kernels ({0, 0} = built-in default;
   // fbst_autotune / fbst_set_shapes change them).
@@ -300,4 +312,11 @@ int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count,
                               float2* pre_r, float2* qspec_r, float2* post_r, cudaStream_t s);
 // In-place FP64 FFT of `rows` contiguous rows of size P (dir -1 forward, +1 unnormalised inverse).
 int fft64_rows(double2* data, int rows, int P, const double2* tw, int dir, cudaStream_t s);
+// Toeplitz generators a_b(d) of the plan's beams in FP64 (Sec. V), [B][L] (plan.cu).
+int plan_toeplitz_generators(fbst_plan_s* p, double2* gen, cudaStream_t s);
+// x = A^{-1} e_0 for `count` generators [count][L] by the Levinson recursion (plan.cu) or by the
+// method of enum fbst_generator_solver (superfast.cu); a non-positive pivot records
+// FBST_ERR_NUMERIC in the plan's status word.
+int launch_levinson(const double2* gen, double2* x, int count, int L, int* status, cudaStream_t s);
+int solve_generators(fbst_plan_s* p, const double2* gen, double2* x, int count, int method, cudaStream_t s);
 }  // namespace fbst

@@ -88,6 +88,8 @@ extern "C" int fbst_derive(const fbst_geometry* g, int M, int N, int B, const fb
   if (!(band->epsilon >= 1.0 && band->epsilon <= 2.0)) return FBST_ERR_INVALID;
   if (!(band->delta > 0.0) || !std::isfinite(band->delta)) return FBST_ERR_INVALID;
   if (band->max_blocks < 1) return FBST_ERR_INVALID;
+  if (band->generator_solver != FBST_GEN_LEVINSON && band->generator_solver != FBST_GEN_SUPERFAST)
+    return FBST_ERR_INVALID;
   switch (band->stage2) {
     case FBST_STAGE2_AUTO: case FBST_STAGE2_GS: case FBST_STAGE2_GS_IR1: case FBST_STAGE2_DENSE_FP32:
     case FBST_STAGE2_DENSE_BF16X3: case FBST_STAGE2_DENSE_TF32: case FBST_STAGE2_DENSE_TF32X3:
@@ -455,13 +457,17 @@ __global__ void k_generators_dir(double2* gen, rat_consts rc, const double* __re
 // alpha = eps*rho*u_b/L, z_m^d by repeated products from z_m^{d0} (FP64 sincospi once per element
 // and warp; the products lose about d ulps), then a warp reduction per d.
 __global__ void __launch_bounds__(256) k_generators_positions(double2* gen, rat_consts rc, const double* __restrict__ pos,
-                                                              int M, int B, double delta) {
+                                                              const double* __restrict__ pos_y, int M, int bx, int by,
+                                                              double delta) {
   extern __shared__ double2 accg[];  // [L]
   const int b = blockIdx.x, L = rc.L;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double eps = (double)rc.en / (double)rc.ed;
   const double rho = (double)rc.fp / (double)(2 * rc.fq + rc.fp);
-  const double alpha = eps * rho * (-1.0 + 2.0 * b / B) / L;
+  // Beam b = bu * by + bv at (u, v) = (-1 + 2 bu / bx, -1 + 2 bv / by); the element's delay per unit
+  // d is alpha_x x_m + alpha_y y_m (y = 0 for a linear array, pos_y = NULL).
+  const double ax = eps * rho * (-1.0 + 2.0 * (b / by) / bx) / L;
+  const double ay = pos_y ? eps * rho * (-1.0 + 2.0 * (b % by) / by) / L : 0.0;
   const int d0 = (int)((long long)L * warp / 8), d1 = (int)((long long)L * (warp + 1) / 8);
   for (int d = d0 + lane; d < d1; d += 32) accg[d] = make_double2(0.0, 0.0);
   __syncwarp();
@@ -469,10 +475,11 @@ __global__ void __launch_bounds__(256) k_generators_positions(double2* gen, rat_
     const int m = m0 + lane;
     double2 z = make_double2(1.0, 0.0), zp = make_double2(0.0, 0.0);
     if (m < M) {
+      const double dly = ax * pos[m] + (pos_y ? ay * pos_y[m] : 0.0);
       double sn, cs;
-      sincospi(-2.0 * alpha * pos[m], &sn, &cs);
+      sincospi(-2.0 * dly, &sn, &cs);
       z = make_double2(cs, sn);
-      sincospi(-2.0 * alpha * pos[m] * d0, &sn, &cs);
+      sincospi(-2.0 * dly * d0, &sn, &cs);
       zp = make_double2(cs, sn);                // z^{d0}
     }
     for (int d = d0; d < d1; ++d) {
@@ -574,6 +581,14 @@ __global__ void k_levinson(const double2* __restrict__ gen, double2* __restrict_
     return;
   }
   for (int i = tid; i < L; i += nth) xout[(size_t)b * L + i] = f[i];
+}
+
+int launch_levinson(const double2* gen, double2* x, int count, int L, int* status, cudaStream_t s) {
+  const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
+  FBST_CUDA_TRY(cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
+  k_levinson<<<count, 256, lev_smem, s>>>(gen, x, L, status);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
 }
 
 // Rows for the Gohberg-Semencul spectra: row 2b = x_b / sqrt(x_0), row 2b+1 = Z J conj(x_b) / sqrt(x_0),
@@ -730,8 +745,9 @@ static void gauss_legendre(int n, double* x, double* w) {
 // Psi(k/nf) = integral psi(s) exp(2*pi*i*(k/nf)*s) ds = W * integral_0^1 phi(z) cos(pi*(k/nf)*W*z) dz
 // (phi even), up to the aliasing error the kernel width sets. Beam b reads mode k = b - B/2; its
 // factor 1/Psi is computed here by 200-point Gauss-Legendre quadrature in FP64 and rounded once.
-int nufft_deconv(fbst_plan_s* p, cudaStream_t s) {
-  const int B = p->info.B, W = p->nu_w, nf = p->nu_nf;
+// 1 / (W * kernel Fourier transform) at the modes b - B/2 of an axis of B beams on an nf-point grid.
+static int nufft_deconv_axis(const fbst_plan_s* p, int B, int nf, float* dst, cudaStream_t s) {
+  const int W = p->nu_w;
   const double beta = nufft_beta(W);
   constexpr int kQ = 200;
   double xq[kQ], wq[kQ];
@@ -747,11 +763,34 @@ int nufft_deconv(fbst_plan_s* p, cudaStream_t s) {
     }
     host[b] = (float)(1.0 / (W * acc));
   }
-  const cudaError_t e = cudaMemcpyAsync(p->nu_deconv, host, sizeof(float) * B, cudaMemcpyHostToDevice, s);
+  const cudaError_t e = cudaMemcpyAsync(dst, host, sizeof(float) * B, cudaMemcpyHostToDevice, s);
   const cudaError_t e2 = cudaStreamSynchronize(s);
   std::free(host);
   FBST_CUDA_TRY(e);
   FBST_CUDA_TRY(e2);
+  return FBST_OK;
+}
+
+int nufft_deconv(fbst_plan_s* p, cudaStream_t s) {
+  if (!p->nu_nfy) return nufft_deconv_axis(p, p->info.B, p->nu_nf, p->nu_deconv, s);
+  FBST_TRY(nufft_deconv_axis(p, p->geom.bx, p->nu_nf, p->nu_deconv, s));
+  return nufft_deconv_axis(p, p->geom.by, p->nu_nfy, p->nu_deconv_y, s);
+}
+
+int plan_toeplitz_generators(fbst_plan_s* p, double2* gen, cudaStream_t s) {
+  const fbst_info& in = p->info;
+  const int L = in.L, B = in.B;
+  rat_consts rc{in.eps_num, in.eps_den, in.fb_num, in.fb_den, in.N, L};
+  if (p->nu_nf) {
+    FBST_CUDA_TRY(cudaFuncSetAttribute(k_generators_positions, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(L * sizeof(double2))));
+    k_generators_positions<<<B, 256, L * sizeof(double2), s>>>(gen, rc, p->pos, p->nu_nfy ? p->pos_y : nullptr, in.M,
+                                                                p->geom.bx, p->geom.by, in.delta);
+  } else {
+    k_generators<<<dim3(grid_for(L, 256) > 64 ? 64 : grid_for(L, 256), B), 256, 0, s>>>(
+        gen, rc, p->geom.bx, p->geom.by, p->geom.mx, p->geom.my, in.delta);
+  }
+  FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
 }
 
@@ -790,8 +829,12 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
 
     // Stage 1b tables: the NUFFT tables of a non-uniform array, else one chirp-z set per axis.
     if (p->nu_nf) {
-      k_nufft_tables<<<grid_for((size_t)L * in.M, 256), 256, 0, s>>>(p->nu_j0, p->nu_dg, rc, p->pos, in.M, B,
-                                                                    p->nu_nf, p->nu_w);
+      // One table per axis: x against the bx beams along u, y against the by beams along v.
+      k_nufft_tables<<<grid_for((size_t)L * in.M, 256), 256, 0, s>>>(p->nu_j0, p->nu_dg, rc, p->pos, in.M,
+                                                                    p->geom.bx, p->nu_nf, p->nu_w);
+      if (p->nu_nfy)
+        k_nufft_tables<<<grid_for((size_t)L * in.M, 256), 256, 0, s>>>(p->nu_j0y, p->nu_dgy, rc, p->pos_y, in.M,
+                                                                      p->geom.by, p->nu_nfy, p->nu_w);
       FBST_CUDA_TRY(cudaGetLastError());
       if ((rc_status = nufft_deconv(p, s)) != FBST_OK) break;
     }
@@ -806,19 +849,9 @@ int build_plan_tables(fbst_plan_s* p, cudaStream_t s) {
     FBST_CUDA_TRY(cudaGetLastError());
 
     // Toeplitz generators (closed form on the grid, direct FP64 sums over a non-uniform array's
-    // positions) and Levinson.
-    if (p->nu_nf) {
-      FBST_CUDA_TRY(cudaFuncSetAttribute(k_generators_positions, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(L * sizeof(double2))));
-      k_generators_positions<<<B, 256, L * sizeof(double2), s>>>(gen, rc, p->pos, in.M, B, in.delta);
-    } else {
-      k_generators<<<dim3(grid_for(L, 256) > 64 ? 64 : grid_for(L, 256), B), 256, 0, s>>>(
-          gen, rc, p->geom.bx, p->geom.by, p->geom.mx, p->geom.my, in.delta);
-    }
-    const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
-    FBST_CUDA_TRY(cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem));
-    k_levinson<<<B, 256, lev_smem, s>>>(gen, p->x64, L, p->d_status);
-    FBST_CUDA_TRY(cudaGetLastError());
+    // positions) and the solve for x_b (Levinson or superfast).
+    if ((rc_status = plan_toeplitz_generators(p, gen, s)) != FBST_OK) break;
+    if ((rc_status = solve_generators(p, gen, p->x64, B, p->band.generator_solver, s)) != FBST_OK) break;
 
     // Gohberg-Semencul spectra (FP64, kept in scratch for the dense build).
     const int Pg = in.P_gs;
@@ -874,18 +907,16 @@ int build_direction_x(fbst_plan_s* p, const double* dirs_dev, int count, double2
   rat_consts rc{in.eps_num, in.eps_den, in.fb_num, in.fb_den, in.N, L};
   double2* gen = nullptr;
   FBST_TRY(plan_alloc_n(p, &gen, (size_t)count * L));
+  if (s != p->mem_stream && cudaStreamSynchronize(p->mem_stream) != cudaSuccess) {
+    plan_free(p, gen);
+    return FBST_ERR_CUDA;
+  }
   const int gx = grid_for(L, 256) > 64 ? 64 : grid_for(L, 256);
   k_generators_dir<<<dim3(gx, count), 256, 0, s>>>(gen, rc, dirs_dev, p->geom.mx, p->geom.my, in.delta);
-  const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem);
-  if (e == cudaSuccess) {
-    k_levinson<<<count, 256, lev_smem, s>>>(gen, x, L, p->d_status);
-    e = cudaGetLastError();
-  }
+  const int r = solve_generators(p, gen, x, count, p->band.generator_solver, s);
   cudaStreamSynchronize(s);
   plan_free(p, gen);
-  FBST_CUDA_TRY(e);
-  return FBST_OK;
+  return r;
 }
 
 int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count, float2* XV, float2* Aspec,
@@ -901,14 +932,11 @@ int build_direction_operators(fbst_plan_s* p, const double* dirs_dev, int count,
     if ((r = plan_alloc_n(p, &rows, (size_t)count * 2 * Pg)) != FBST_OK) break;
     if (Aspec && (r = plan_alloc_n(p, &arows, (size_t)count * Pg)) != FBST_OK) break;
     if ((r = plan_alloc_n(p, &qrows, (size_t)in.S_rec * in.P_rec)) != FBST_OK) break;
+    // Allocated in stream order on the plan's stream: make the blocks usable on `s`.
+    if (s != p->mem_stream && cudaStreamSynchronize(p->mem_stream) != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     const int gx = grid_for(L, 256) > 64 ? 64 : grid_for(L, 256);
     k_generators_dir<<<dim3(gx, count), 256, 0, s>>>(gen, rc, dirs_dev, p->geom.mx, p->geom.my, in.delta);
-    const size_t lev_smem = (2 * (size_t)L + 32) * sizeof(double2);
-    if (cudaFuncSetAttribute(k_levinson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lev_smem) != cudaSuccess) {
-      r = FBST_ERR_CUDA;
-      break;
-    }
-    k_levinson<<<count, 256, lev_smem, s>>>(gen, x, L, p->d_status);
+    if ((r = solve_generators(p, gen, x, count, p->band.generator_solver, s)) != FBST_OK) break;
     k_gs_rows<<<dim3(grid_for(Pg, 256) > 64 ? 64 : grid_for(Pg, 256), count), 256, 0, s>>>(x, rows, L, Pg, p->d_status);
     if (cudaGetLastError() != cudaSuccess) { r = FBST_ERR_CUDA; break; }
     if ((r = fft64_rows(rows, 2 * count, Pg, p->tw64, -1, s)) != FBST_OK) break;

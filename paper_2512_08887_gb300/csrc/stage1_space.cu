@@ -394,8 +394,193 @@ static int launch_space_nufft(const fbst_plan_s* p, const float2* yhat, float2* 
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Non-uniform rectangular array (Sec. IX, Eq. (16) with both coordinates off the grid): the element
+// sum of each frequency as a two-dimensional type-1 NUFFT. The oversampled grid has NFX x NFY
+// points (NFX >= 2 bx, NFY >= 2 by); element m lands at grid coordinates (gx, gy) = (NFX 2 kappa
+// x_m / bx, NFY 2 kappa y_m / by) (tables from plan.cu, one per axis) and is spread over W x W
+// points with the product of the two one-dimensional kernels; the positions move independently in
+// both axes, so the spreading does not separate into two one-dimensional passes. Then the 2-D
+// unnormalised inverse-sign FFT: an NFY-point FFT along every row of the grid, and an NFX-point
+// FFT along the by columns whose y-modes are beams; beam (bu, bv) (b = bu by + bv) is read at mode
+// (bu - bx/2, bv - by/2) times the two axes' deconvolution factors. A CTA takes G consecutive
+// frequencies of one block in turn; the [B][G] tile leaves in G-frequency runs. The grid rows are
+// padded by one float (NFY + 1) so that the column FFT's strided loads fall on distinct banks.
+// FFT groups: T = min(32, NF/2) threads (inside one warp: warp barriers), E = NF/T points each;
+// every group makes the same number of transforms (a group past the last row or column transforms
+// zeros and stores nothing), as the warp barriers need.
+// ---------------------------------------------------------------------------------------------
+constexpr int kNu2Threads = 256;
+constexpr int kNu2G = 4;
+
+template <int NF> struct nu2_shape {
+  static constexpr int T = NF / 2 < 32 ? NF / 2 : 32;
+  static constexpr int E = NF / T;
+};
+
+template <int NFX, int NFY>
+__global__ void __launch_bounds__(kNu2Threads)
+k_nufft_space_2d(const float2* __restrict__ yhat, float2* __restrict__ w, const int* __restrict__ j0x,
+                 const float* __restrict__ dgx, const int* __restrict__ j0y, const float* __restrict__ dgy,
+                 const float* __restrict__ deconv_x, const float* __restrict__ deconv_y,
+                 const float2* __restrict__ tw, int M, int bx, int by, int L, int W, float beta, int nblk) {
+  constexpr int RS = NFY + 1;  // padded row stride of the grid
+  constexpr int TY = nu2_shape<NFY>::T, EY = nu2_shape<NFY>::E;
+  constexpr int TX = nu2_shape<NFX>::T, EX = nu2_shape<NFX>::E;
+  constexpr int GY = kNu2Threads / TY, GX = kNu2Threads / TX;  // FFT groups per CTA
+  constexpr int XB = (GY * NFY > GX * NFX) ? GY * NFY : GX * NFX;
+  extern __shared__ float2 sm[];
+  float* gre = reinterpret_cast<float*>(sm);
+  float* gim = gre + NFX * RS;
+  float2* xbuf = sm + NFX * RS;   // FFT exchange buffers (after the two float planes)
+  float2* tile = xbuf + XB;       // [B][kNu2G + 1]
+  const int B = bx * by;
+  const int tid = threadIdx.x;
+  const float inv_half = 2.0f / W;
+  long long it0, it1;
+  my_range((long long)((L + kNu2G - 1) / kNu2G) * nblk, &it0, &it1);
+  for (long long it = it0; it < it1; ++it) {
+    const int lt = (int)(it / nblk), blk = (int)(it % nblk);
+    const int ell0 = lt * kNu2G;
+    for (int g = 0; g < kNu2G && ell0 + g < L; ++g) {
+      const int ell = ell0 + g;
+      for (int i = tid; i < NFX * RS; i += kNu2Threads) {
+        gre[i] = 0.f;
+        gim[i] = 0.f;
+      }
+      __syncthreads();
+      const float2* row = yhat + ((size_t)blk * L + ell) * M;
+      const int* jxr = j0x + (size_t)ell * M;
+      const int* jyr = j0y + (size_t)ell * M;
+      const float* dxr = dgx + (size_t)ell * M;
+      const float* dyr = dgy + (size_t)ell * M;
+      for (int m = tid; m < M; m += kNu2Threads) {
+        const float2 c = row[m];
+        const int jx = jxr[m], jy = jyr[m];
+        const float dx = dxr[m], dy = dyr[m];
+        float ky[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float z = ((float)q - dy) * inv_half, z2 = z * z;
+          ky[q] = (q < W && z2 < 1.f) ? expf(-beta * z2 / (1.f + sqrtf(1.f - z2))) : 0.f;
+        }
+        for (int qx = 0; qx < W; ++qx) {
+          const float z = ((float)qx - dx) * inv_half, z2 = z * z;
+          const float kx = z2 < 1.f ? expf(-beta * z2 / (1.f + sqrtf(1.f - z2))) : 0.f;
+          const float cr = c.x * kx, ci = c.y * kx;
+          const int base = ((jx + qx) & (NFX - 1)) * RS;
+#pragma unroll
+          for (int qy = 0; qy < 16; ++qy) {
+            if (qy < W) {
+              const int j = base + ((jy + qy) & (NFY - 1));
+              atomicAdd(&gre[j], cr * ky[qy]);
+              atomicAdd(&gim[j], ci * ky[qy]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      {  // NFY-point transforms along the NFX rows
+        const int grp = tid / TY, t = tid % TY;
+        float2* fb = xbuf + grp * NFY;
+        for (int r0 = 0; r0 < NFX; r0 += GY) {
+          const int rr = r0 + grp;
+          float2 v[1][EY];
+#pragma unroll
+          for (int r = 0; r < EY; ++r) {
+            const int j = t + TY * r;
+            v[0][r] = rr < NFX ? make_float2(gre[rr * RS + j], gim[rr * RS + j]) : make_float2(0.f, 0.f);
+          }
+          block_fft<NFY, EY, 1, +1>(v, fb, tw, t, 1 + (grp & 15));
+          if (rr < NFX) {
+#pragma unroll
+            for (int r = 0; r < EY; ++r) {
+              const int j = t + TY * r;
+              gre[rr * RS + j] = v[0][r].x;
+              gim[rr * RS + j] = v[0][r].y;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      {  // NFX-point transforms along the by columns that hold beams
+        const int grp = tid / TX, t = tid % TX;
+        float2* fb = xbuf + grp * NFX;
+        for (int c0 = 0; c0 < by; c0 += GX) {
+          const int bv = c0 + grp;
+          const int col = ((bv - by / 2) + NFY) & (NFY - 1);
+          float2 v[1][EX];
+#pragma unroll
+          for (int r = 0; r < EX; ++r) {
+            const int j = t + TX * r;
+            v[0][r] = bv < by ? make_float2(gre[j * RS + col], gim[j * RS + col]) : make_float2(0.f, 0.f);
+          }
+          block_fft<NFX, EX, 1, +1>(v, fb, tw, t, 1 + (grp & 15));
+          if (bv < by) {
+            const float sy = deconv_y[bv];
+#pragma unroll
+            for (int r = 0; r < EX; ++r) {
+              const int k = t + TX * r;
+              const int bu = (k < NFX / 2 ? k : k - NFX) + bx / 2;
+              if (bu >= 0 && bu < bx) tile[(bu * by + bv) * (kNu2G + 1) + g] = cscale(v[0][r], deconv_x[bu] * sy);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    float2* out = w + (size_t)blk * B * L + ell0;
+    for (int idx = tid; idx < B * kNu2G; idx += kNu2Threads) {
+      const int b = idx / kNu2G, gg = idx % kNu2G;
+      if (ell0 + gg < L) out[(size_t)b * L + gg] = tile[b * (kNu2G + 1) + gg];
+    }
+    __syncthreads();
+  }
+}
+
+template <int NFX, int NFY>
+static int run_nufft_2d(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  constexpr int RS = NFY + 1;
+  constexpr int GY = kNu2Threads / nu2_shape<NFY>::T, GX = kNu2Threads / nu2_shape<NFX>::T;
+  constexpr int XB = (GY * NFY > GX * NFX) ? GY * NFY : GX * NFX;
+  const fbst_info& in = p->info;
+  if (p->nu_w > 16) return FBST_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(float) * 2 * NFX * RS + sizeof(float2) * ((size_t)XB + (size_t)in.B * (kNu2G + 1));
+  if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
+  FBST_TRY(allow_max_smem(k_nufft_space_2d<NFX, NFY>));
+  const long long items = (long long)((in.L + kNu2G - 1) / kNu2G) * nblk;
+  const int grid = grid_for_items(items, resident_ctas(k_nufft_space_2d<NFX, NFY>, kNu2Threads, smem));
+  k_nufft_space_2d<NFX, NFY><<<grid, kNu2Threads, smem, s>>>(
+      yhat, w, p->nu_j0, p->nu_dg, p->nu_j0y, p->nu_dgy, p->nu_deconv, p->nu_deconv_y, p->tw32, in.M, p->geom.bx,
+      p->geom.by, in.L, p->nu_w, (float)nufft_beta(p->nu_w), nblk);
+  FBST_CUDA_TRY(cudaGetLastError());
+  return FBST_OK;
+}
+
+template <int NFX>
+static int launch_nufft_2d_x(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  switch (p->nu_nfy) {
+    case 16: return run_nufft_2d<NFX, 16>(p, yhat, w, nblk, s);
+    case 32: return run_nufft_2d<NFX, 32>(p, yhat, w, nblk, s);
+    case 64: return run_nufft_2d<NFX, 64>(p, yhat, w, nblk, s);
+    case 128: return run_nufft_2d<NFX, 128>(p, yhat, w, nblk, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
+static int launch_space_nufft_2d(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, cudaStream_t s) {
+  switch (p->nu_nf) {
+    case 16: return launch_nufft_2d_x<16>(p, yhat, w, nblk, s);
+    case 32: return launch_nufft_2d_x<32>(p, yhat, w, nblk, s);
+    case 64: return launch_nufft_2d_x<64>(p, yhat, w, nblk, s);
+    case 128: return launch_nufft_2d_x<128>(p, yhat, w, nblk, s);
+    default: return FBST_ERR_UNSUPPORTED;
+  }
+}
+
 static int czt_space(const fbst_plan_s* p, const float2* yhat, float2* w, int nblk, unsigned* wmax, cudaStream_t s) {
   if (nblk <= 0) return FBST_OK;
+  if (p->nu_nf && p->nu_nfy) return launch_space_nufft_2d(p, yhat, w, nblk, s);
   if (p->nu_nf) return launch_space_nufft(p, yhat, w, nblk, s);
   if (p->geom.kind == FBST_ULA) {
     job_list<space_job> jl;

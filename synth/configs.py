@@ -12,6 +12,8 @@ ULA1024 linear array M=1024, N=512, B=1024, fb=0.5 (L=1024); K=8 plane waves, 10
     array (M = B = 1024) at which the transform's roofline is stated.
 NU1024 the ULA1024 signal on the same array with every element but the first moved by N(0, 0.2^2)
     half wavelengths along the axis (position seed 11): a non-uniform array (Sec. IX).
+NUC3 the C3 signal on the same 32x32 array with every element but the first moved by N(0, 0.2^2)
+    half wavelengths in both coordinates (position seed 12): a non-uniform rectangular array.
 C2N the C2 array and grid with one unit-power source on grid beam 160 and two interferers on grid
     beams 64 and 96 at 20 dB above it, 10 dB SNR, 64 blocks; seed 1005. Workload of the beamspace
     interference nulling (Sec. VIII-B), which removes beams 64 and 96.
@@ -29,6 +31,8 @@ CONFIGS = {
                     nblk=64, Q=64),
     "NU1024": dict(kind="ula", mx=1024, my=1, bx=1024, by=1, N=512, frac_bw=0.5, K=8, snr_db=10.0, seed=2024,
                    nblk=64, Q=64, sigma=0.2, pos_seed=11),
+    "NUC3": dict(kind="ura", mx=32, my=32, bx=32, by=32, N=512, frac_bw=0.3, K=16, snr_db=10.0, seed=1003,
+                 nblk=16, sigma=0.2, pos_seed=12),
 }
 
 
@@ -54,7 +58,8 @@ def config_data(name: str, nblk: int | None = None, Q: int | None = None, first_
         d = ula_config(c["mx"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q,
                        first_block=first_block, geom=config_geometry(name))
     else:
-        d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q)
+        d = ura_config(c["mx"], c["my"], c["N"], c["nblk"], c["frac_bw"], c["K"], c["snr_db"], c["seed"], Q=Q,
+                       geom=config_geometry(name))
     d.update(c)
     return d
 

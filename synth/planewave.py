@@ -166,11 +166,12 @@ def ula_config(M: int, N: int, nblk: int, frac_bw: float, K: int, snr_db: float 
 
 
 def ura_config(mx: int, my: int, N: int, nblk: int, frac_bw: float, K: int, snr_db: float | None,
-               seed: int, Q: int = 256) -> dict:
-    """Same as ula_config for an mx-by-my rectangular array, sources uniform over the unit disk."""
+               seed: int, Q: int = 256, geom: ArrayGeometry | None = None) -> dict:
+    """Same as ula_config for an mx-by-my rectangular array, sources uniform over the unit disk;
+    `geom` may move the elements off the grid (the same sources, delays at the actual positions)."""
     ss = np.random.SeedSequence(seed)
     rs, rn = (np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(2))
-    geom = ArrayGeometry("ura", mx, my)
+    geom = geom if geom is not None else ArrayGeometry("ura", mx, my)
     src = draw_sources(rs, K, "ura", Q)
     rec = array_record(geom, src, frac_bw, nblk * N, snr_db, rn)
     return {"geom": geom, "sources": src, "frac_bw": frac_bw, "N": N, "nblk": nblk,

@@ -105,3 +105,19 @@ def test_nulling_entry_points_check_arguments_before_any_cuda_call(lib):
     assert lib.fbst_null_execute(None, None, None, 1, None) == -1
     assert lib.fbst_null_launch_count(None, 4) == 0
     assert lib.fbst_null_destroy(None) == 0
+
+
+def test_generator_solver_field_is_checked(lib):
+    for name in ("levinson", "superfast"):
+        assert fb.derive(fb.make_geometry("ula", 8), 16, fb.make_band(0.5, generator_solver=name)).L == 32
+    band = fb.make_band(0.5)
+    band.generator_solver = 2
+    with pytest.raises(fb.FBSTError) as e:
+        fb.derive(fb.make_geometry("ula", 8), 16, band)
+    assert e.value.status == -1
+
+
+def test_trace_and_generator_entry_points_check_arguments_before_any_cuda_call(lib):
+    assert lib.fbst_trace_stages(None, 4) == -1
+    assert lib.fbst_trace_read(None, None, 0) == -1
+    assert lib.fbst_solve_generators(None, 0, None, None) == -1

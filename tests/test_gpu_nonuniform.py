@@ -138,8 +138,8 @@ def test_invalid_positions_are_rejected():
     with pytest.raises(fb.FBSTError) as e:
         fb.Plan(fb.make_geometry("ula", 8), 16, band, positions=bad)
     assert e.value.status == -1
-    with pytest.raises(fb.FBSTError) as e:
-        fb.Plan(fb.make_geometry("ura", 2, 2), 16, band, positions=np.zeros((4, 2)))
+    with pytest.raises(fb.FBSTError) as e:   # a 256 x 256 oversampled grid: beyond the 2-D kernel
+        fb.Plan(fb.make_geometry("ura", 2, 2, 128, 128), 16, band, positions=np.zeros((4, 2)))
     assert e.value.status == -4
     nu = fb.Plan(fb.make_geometry("ula", 8), 16, band, positions=np.stack([np.arange(8.0), np.zeros(8)], axis=1))
     with pytest.raises(fb.FBSTError) as e:
