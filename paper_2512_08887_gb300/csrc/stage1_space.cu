@@ -14,7 +14,10 @@
 namespace fbst {
 
 // At least 512 threads per SM (128 registers a thread): the kernel lives on latency hiding.
-template <int P, int E, int G>
+// HALF: every job has M = B = P/2, so element i < M and beam b < B are exactly the slots r < E/2
+// of each thread; the zero upper half of the input and the unused upper half of the output are
+// then known at compile time (the first forward pass and the last inverse pass lose that work).
+template <int P, int E, int G, bool HALF>
 __global__ void __launch_bounds__(G * (P / E), G * (P / E) >= 512 ? 1 : 512 / (G * (P / E)))
 k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __restrict__ tw, int max_B) {
   constexpr int T = P / E;
@@ -56,15 +59,15 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 #pragma unroll
         for (int r = 0; r < E; ++r) {
           const int i = t + T * r;
-          pr[r] = i < M ? J.pre[(size_t)ellc * M + i] : make_float2(0.f, 0.f);
+          pr[r] = (HALF ? r < E / 2 : i < M) ? J.pre[(size_t)ellc * M + i] : make_float2(0.f, 0.f);
           ks[r] = J.kspec[(size_t)ellc * P + i];
-          po[r] = i < B ? J.post[(size_t)ellc * B + i] : make_float2(0.f, 0.f);
+          po[r] = (HALF ? r < E / 2 : i < B) ? J.post[(size_t)ellc * B + i] : make_float2(0.f, 0.f);
         }
       }
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
-        v[0][r] = i < M ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
+        v[0][r] = (HALF ? r < E / 2 : i < M) ? cmul(row[i], pr[r]) : make_float2(0.f, 0.f);
       }
       block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
@@ -73,7 +76,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int b = t + T * r;
-        if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], po[r]);
+        if (HALF ? r < E / 2 : b < B) tile[b * (G + 1) + g] = cmul(v[0][r], po[r]);
       }
     } else {
       // Radix 16 has no registers to spare: the rows are read from L1 where they are used.
@@ -83,7 +86,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
-        v[0][r] = i < M ? cmul(row[i], pre[i]) : make_float2(0.f, 0.f);
+        v[0][r] = (HALF ? r < E / 2 : i < M) ? cmul(row[i], pre[i]) : make_float2(0.f, 0.f);
       }
       block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
 #pragma unroll
@@ -92,7 +95,7 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int b = t + T * r;
-        if (b < B) tile[b * (G + 1) + g] = cmul(v[0][r], post[b]);
+        if (HALF ? r < E / 2 : b < B) tile[b * (G + 1) + g] = cmul(v[0][r], post[b]);
       }
     }
     __syncthreads();
@@ -121,17 +124,24 @@ k_czt_space_ula(const __grid_constant__ job_list<space_job> jl, const float2* __
   }
 }
 
-template <int P, int E, int G>
+template <int P, int E, int G, bool HALF>
 static int run_space(const job_list<space_job>& jl, int max_B, const float2* tw, cudaStream_t s) {
   constexpr int T = P / E;
   const size_t wm = (jl.n == 1 && jl.job[0].wmax) ? sizeof(unsigned) * (size_t)jl.job[0].nblk : 0;
   const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_B * (G + 1)) + wm;
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
-  FBST_TRY(allow_max_smem(k_czt_space_ula<P, E, G>));
-  const int grid = grid_for_items(jl.total, resident_ctas(k_czt_space_ula<P, E, G>, G * T, smem));
-  k_czt_space_ula<P, E, G><<<grid, G * T, smem, s>>>(jl, tw, max_B);
+  FBST_TRY(allow_max_smem(k_czt_space_ula<P, E, G, HALF>));
+  const int grid = grid_for_items(jl.total, resident_ctas(k_czt_space_ula<P, E, G, HALF>, G * T, smem));
+  k_czt_space_ula<P, E, G, HALF><<<grid, G * T, smem, s>>>(jl, tw, max_B);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
+}
+
+// Every job of the list has M = B = P/2 (the compile-time half-size form applies).
+static bool space_jobs_half(const job_list<space_job>& jl, int P) {
+  for (int i = 0; i < jl.n; ++i)
+    if (2 * jl.job[i].M != P || 2 * jl.job[i].B != P) return false;
+  return true;
 }
 
 // Compiled shapes (P, E, G); the first entry of each P is its default.
@@ -144,8 +154,12 @@ static int run_space(const job_list<space_job>& jl, int max_B, const float2* tw,
 int launch_space_jobs(const job_list<space_job>& jl, int P, fft_shape sh, int max_B, const float2* tw,
                       cudaStream_t s) {
   if (jl.total <= 0) return FBST_OK;
-#define FBST_X(p, e, g) \
-  if (P == p && sh.E == e && sh.G == g) return run_space<p, e, g>(jl, max_B, tw, s);
+  // The half-size form is compiled for the radix-16 shapes (the defaults of the large transforms).
+  const bool half = space_jobs_half(jl, P);
+#define FBST_X(p, e, g)                                                                               \
+  if (P == p && sh.E == e && sh.G == g)                                                               \
+    return (half && e == 16) ? run_space<p, e, g, (e == 16)>(jl, max_B, tw, s)                        \
+                             : run_space<p, e, g, false>(jl, max_B, tw, s);
   FBST_SPACE_SHAPES(FBST_X)
 #undef FBST_X
   return FBST_ERR_UNSUPPORTED;

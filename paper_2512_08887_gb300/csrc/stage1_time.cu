@@ -17,7 +17,10 @@
 
 namespace fbst {
 
-template <int P, int E, int G>
+// HALF: every job has N = L/S = P/2, so snapshot n < N and output i < L/S are exactly the slots
+// r < E/2 of each thread (the zero upper half of the input and the unused upper half of each
+// output are known at compile time).
+template <int P, int E, int G, bool HALF>
 __global__ void __launch_bounds__(G * (P / E))
 k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restrict__ tw) {
   constexpr int T = P / E;
@@ -43,7 +46,7 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
 #pragma unroll
     for (int r = 0; r < E; ++r) {
       const int n = t + T * r;
-      v[0][r] = (n < N && m < M) ? cmul(yrow[n], J.pre[n]) : make_float2(0.f, 0.f);
+      v[0][r] = ((HALF ? r < E / 2 : n < N) && m < M) ? cmul(yrow[n], J.pre[n]) : make_float2(0.f, 0.f);
     }
     block_fft<P, E, 1, -1>(v, fbuf, tw, t, 1 + g);
     for (int h = 0; h < S; ++h) {
@@ -54,7 +57,7 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int i = t + T * r;
-        if (i < Lh) tile[i * (G + 1) + g] = cmul(u[0][r], J.post[h * Lh + i]);
+        if (HALF ? r < E / 2 : i < Lh) tile[i * (G + 1) + g] = cmul(u[0][r], J.post[h * Lh + i]);
       }
       __syncthreads();
       float2* out = J.yhat + ((size_t)blk * L + (size_t)h * Lh) * M + m0;
@@ -67,16 +70,23 @@ k_czt_time(const __grid_constant__ job_list<time_job> jl, const float2* __restri
   }
 }
 
-template <int P, int E, int G>
+template <int P, int E, int G, bool HALF>
 static int run_time(const job_list<time_job>& jl, int max_Lh, const float2* tw, cudaStream_t s) {
   constexpr int T = P / E;
   const size_t smem = sizeof(float2) * ((size_t)G * fft_smem_elems<float2>(P) + (size_t)max_Lh * (G + 1));
   if (smem > kMaxSmem) return FBST_ERR_UNSUPPORTED;
-  FBST_TRY(allow_max_smem(k_czt_time<P, E, G>));
-  const int grid = grid_for_items(jl.total, resident_ctas(k_czt_time<P, E, G>, G * T, smem));
-  k_czt_time<P, E, G><<<grid, G * T, smem, s>>>(jl, tw);
+  FBST_TRY(allow_max_smem(k_czt_time<P, E, G, HALF>));
+  const int grid = grid_for_items(jl.total, resident_ctas(k_czt_time<P, E, G, HALF>, G * T, smem));
+  k_czt_time<P, E, G, HALF><<<grid, G * T, smem, s>>>(jl, tw);
   FBST_CUDA_TRY(cudaGetLastError());
   return FBST_OK;
+}
+
+// Every job of the list has N = L/S = P/2 (the compile-time half-size form applies).
+static bool time_jobs_half(const job_list<time_job>& jl, int P) {
+  for (int i = 0; i < jl.n; ++i)
+    if (2 * jl.job[i].N != P || 2 * (jl.job[i].L / jl.job[i].S) != P) return false;
+  return true;
 }
 
 // Compiled shapes (P, E, G): G*P/E <= 512 threads. The first entry of each P is its default.
@@ -89,8 +99,12 @@ static int run_time(const job_list<time_job>& jl, int max_Lh, const float2* tw, 
 int launch_time_jobs(const job_list<time_job>& jl, int P, fft_shape sh, int max_Lh, const float2* tw,
                      cudaStream_t s) {
   if (jl.total <= 0) return FBST_OK;
-#define FBST_X(p, e, g) \
-  if (P == p && sh.E == e && sh.G == g) return run_time<p, e, g>(jl, max_Lh, tw, s);
+  // The half-size form is compiled for the radix-16 shapes (the defaults of the large transforms).
+  const bool half = time_jobs_half(jl, P);
+#define FBST_X(p, e, g)                                                                               \
+  if (P == p && sh.E == e && sh.G == g)                                                               \
+    return (half && e == 16) ? run_time<p, e, g, (e == 16)>(jl, max_Lh, tw, s)                        \
+                             : run_time<p, e, g, false>(jl, max_Lh, tw, s);
   FBST_TIME_SHAPES(FBST_X)
 #undef FBST_X
   return FBST_ERR_UNSUPPORTED;

@@ -145,7 +145,8 @@ template <int P> struct sf_shape {
 // s1 steps: [phi, psi] Theta_left on the node's coefficients s1 .. s - 1, written to the right
 // child's windows PhiR, PsiR from index 0. T1: the left child's four polynomials (n1 = s1 + 1
 // coefficients, stride len1). Shared memory: 2P exchange + 3P held spectra.
-template <int P>
+// MINB only separates the copies compiled for the two register budgets of k_superfast.
+template <int P, int MINB>
 __device__ __noinline__ void sf_update(const double2* Phi, const double2* Psi, int a, int s, int s1,
                                        const double2* T1, int len1, double2* PhiR, double2* PsiR, double2* smem,
                                        const double2* __restrict__ tw, int t) {
@@ -210,7 +211,7 @@ __device__ __noinline__ void sf_update(const double2* Phi, const double2* Psi, i
 // strides len1, len2), written with s + 1 coefficients at stride len. Shared memory: 2P exchange +
 // 4P held spectra of T2. P >= s; when P == s the circular product wraps only the degree-s
 // coefficient of column 1, onto its (zero) constant term.
-template <int P>
+template <int P, int MINB>
 __device__ __noinline__ void sf_product(const double2* T1, int n1, int len1, const double2* T2, int n2, int len2, double2* out,
                            int len, int s, double2* smem, const double2* __restrict__ tw, int t) {
   constexpr int E = sf_shape<P>::E, T = sf_shape<P>::T;
@@ -274,27 +275,29 @@ __device__ __noinline__ void sf_product(const double2* T1, int n1, int len1, con
   }
 }
 
+template <int MINB>
 __device__ void sf_update_any(int P, const double2* Phi, const double2* Psi, int a, int s, int s1, const double2* T1,
                               int len1, double2* PhiR, double2* PsiR, double2* smem, const double2* tw, int t) {
   switch (P) {
-    case 64: sf_update<64>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
-    case 128: sf_update<128>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
-    case 256: sf_update<256>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
-    case 512: sf_update<512>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
-    case 1024: sf_update<1024>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
-    default: sf_update<2048>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    case 64: sf_update<64, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    case 128: sf_update<128, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    case 256: sf_update<256, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    case 512: sf_update<512, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    case 1024: sf_update<1024, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
+    default: sf_update<2048, MINB>(Phi, Psi, a, s, s1, T1, len1, PhiR, PsiR, smem, tw, t); break;
   }
 }
 
+template <int MINB>
 __device__ void sf_product_any(int P, const double2* T1, int n1, int len1, const double2* T2, int n2, int len2,
                                double2* out, int len, int s, double2* smem, const double2* tw, int t) {
   switch (P) {
-    case 64: sf_product<64>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
-    case 128: sf_product<128>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
-    case 256: sf_product<256>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
-    case 512: sf_product<512>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
-    case 1024: sf_product<1024>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
-    default: sf_product<2048>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    case 64: sf_product<64, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    case 128: sf_product<128, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    case 256: sf_product<256, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    case 512: sf_product<512, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    case 1024: sf_product<1024, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
+    default: sf_product<2048, MINB>(T1, n1, len1, T2, n2, len2, out, len, s, smem, tw, t); break;
   }
 }
 
@@ -307,7 +310,11 @@ struct sf_frame {
 
 // gen: [count][L] generators a(d) (first column c[d] = conj(a(d))); x: [count][L]; ws: gridDim.x
 // slots of ws_elems. Writes FBST_ERR_NUMERIC to *status if a pivot is not positive.
-__global__ void __launch_bounds__(kSfThreads, 2)
+// MINB: resident CTAs per SM the register budget is cut for (2 up to L = 1025, whose FFTs of at
+// most 1024 points need 96 KB of shared memory; 1 beyond, where 192 KB allow one CTA per SM anyway
+// and the 2048-point products get the registers they need).
+template <int MINB>
+__global__ void __launch_bounds__(kSfThreads, MINB)
     k_superfast(const double2* __restrict__ gen, double2* __restrict__ xout, int L, int count, double2* ws_all,
                 size_t ws_elems, const double2* __restrict__ tw, int* status) {
   extern __shared__ double2 sf_smem[];
@@ -363,12 +370,12 @@ __global__ void __launch_bounds__(kSfThreads, 2)
         st[++top] = sf_frame{f.a, m, 0, 0, f.wb, f.wbase};
       } else if (f.phase == 1) {
         double2* Rphi = ws + sf_win_off(L, l + 1);
-        sf_update_any(P, Wphi, Wpsi, ar, s, s1, T1, len1, Rphi, Rphi + sf_win_len(L, l + 1), sf_smem, tw, t);
+        sf_update_any<MINB>(P, Wphi, Wpsi, ar, s, s1, T1, len1, Rphi, Rphi + sf_win_len(L, l + 1), sf_smem, tw, t);
         __syncthreads();
         st[top].phase = 2;
         st[++top] = sf_frame{m, f.b, 0, 1, l + 1, m};
       } else {
-        sf_product_any(P, T1, s1 + 1, len1, sf_slot(ws, L, l + 1, 1), s - s1 + 1, len1, out, len, s, sf_smem, tw, t);
+        sf_product_any<MINB>(P, T1, s1 + 1, len1, sf_slot(ws, L, l + 1, 1), s - s1 + 1, len1, out, len, s, sf_smem, tw, t);
         __syncthreads();
         --top;
       }
@@ -406,12 +413,16 @@ int solve_generators(fbst_plan_s* p, const double2* gen, double2* x, int count, 
   if (method != FBST_GEN_SUPERFAST) return FBST_ERR_INVALID;
   if (L - 1 > 2048 || sf_depth(L) > kSfMaxDepth) return FBST_ERR_UNSUPPORTED;
   const size_t smem = superfast_smem_bytes(L);
-  // The largest dynamic shared memory any plan needs (L - 1 <= 2048: P = 2048), below the 227 KB
+  // The largest dynamic shared memory each form needs (P = 1024 and P = 2048), below the 227 KB
   // opt-in limit less the kernel's static shared word.
-  static const cudaError_t attr = cudaFuncSetAttribute(k_superfast, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)superfast_smem_bytes(2049));
-  FBST_CUDA_TRY(attr);
-  const int ctas = grid_for_items(count, resident_ctas(k_superfast, kSfThreads, smem));
+  static const cudaError_t attr2 = cudaFuncSetAttribute(k_superfast<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)superfast_smem_bytes(1025));
+  static const cudaError_t attr1 = cudaFuncSetAttribute(k_superfast<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)superfast_smem_bytes(2049));
+  const bool big = L - 1 > 1024;
+  FBST_CUDA_TRY(big ? attr1 : attr2);
+  const int ctas = grid_for_items(count, big ? resident_ctas(k_superfast<1>, kSfThreads, smem)
+                                             : resident_ctas(k_superfast<2>, kSfThreads, smem));
   const size_t elems = sf_ws_elems(L);
   double2* ws = nullptr;
   FBST_TRY(plan_alloc_n(p, &ws, (size_t)ctas * elems));
@@ -420,7 +431,8 @@ int solve_generators(fbst_plan_s* p, const double2* gen, double2* x, int count, 
   const bool other = s != p->mem_stream;
   cudaError_t e = other ? cudaStreamSynchronize(p->mem_stream) : cudaSuccess;
   if (e == cudaSuccess) {
-    k_superfast<<<ctas, kSfThreads, smem, s>>>(gen, x, L, count, ws, elems, p->tw64, p->d_status);
+    if (big) k_superfast<1><<<ctas, kSfThreads, smem, s>>>(gen, x, L, count, ws, elems, p->tw64, p->d_status);
+    else k_superfast<2><<<ctas, kSfThreads, smem, s>>>(gen, x, L, count, ws, elems, p->tw64, p->d_status);
     e = cudaGetLastError();
   }
   if (other) cudaStreamSynchronize(s);
