@@ -974,6 +974,37 @@ def run_reference_offgrid(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_reference_gen(args) -> None:
+    """Reference arm of GEN: the oracle's generators, a dense FP64 solve of each beam's Gram matrix
+    built by direct sums (Eq. (5)), for 2 beams per step of the same 1024-element ULA plan."""
+    import oracle as O
+    M, N = 1024, args.gen_n
+    pb = O.make_problem("ula", M, 1, M, 1, N, frac_bw=0.5, epsilon=1.01, delta_rel=1e-3)
+    L = pb.L
+    beams = [0, M // 2 + 1]
+    e0 = np.eye(L)[:, 0]
+    for _ in range(args.warmup):
+        np.linalg.solve(O.gram(pb, beams[0]), e0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for b in beams:
+            np.linalg.solve(O.gram(pb, b), e0)
+        times.append(time.perf_counter() - t0)
+    value = len(beams) * len(times) / sum(times)
+    unit = "systems/s"
+    line = {"impl": "reference", "metric": "Toeplitz generator systems solved/s (FP64, rel err vs dense solve)",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"GEN oracle sample: ULA M={M} N={N} L={L}, {len(beams)} systems per step"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"per step: the Gram matrices of {len(beams)} beams by direct sums and their "
+                                       "dense FP64 solves (numpy)"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -983,6 +1014,9 @@ def run_reference(args) -> None:
         return
     if args.workload == "OG":
         run_reference_offgrid(args)
+        return
+    if args.workload == "GEN":
+        run_reference_gen(args)
         return
     if args.workload == "STREAM":
         # The streamed transform is the per-block transform of the same array on overlapping blocks;
