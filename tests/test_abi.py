@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2512_08887_gb300 as fb
@@ -121,3 +122,26 @@ def test_trace_and_generator_entry_points_check_arguments_before_any_cuda_call(l
     assert lib.fbst_trace_stages(None, 4) == -1
     assert lib.fbst_trace_read(None, None, 0) == -1
     assert lib.fbst_solve_generators(None, 0, None, None) == -1
+
+
+def test_positions_are_checked_before_any_cuda_call(lib):
+    # fbst_plan_positions (Sec. IX) validates the element positions and the 2-D NUFFT's size on the
+    # host, before it touches the device.
+    def call(kind, mx, my, bx, by, pos):
+        g = fb.make_geometry(kind, mx, my, bx, by)
+        arr = (C.c_double * pos.size)(*pos.ravel().tolist())
+        h = C.c_void_p()
+        return lib.fbst_plan_positions(C.byref(h), C.byref(g), arr, mx * my, 16, bx * by,
+                                       C.byref(fb.make_band(0.5)), None, None, None, None), h
+    grid = np.stack([np.arange(8.0), np.zeros(8)], axis=1)
+    bad = grid.copy()
+    bad[3, 0] = np.inf
+    assert call("ula", 8, 1, 8, 1, bad)[0] == -1                  # not finite
+    bad = grid.copy()
+    bad[2, 1] = 0.25
+    assert call("ula", 8, 1, 8, 1, bad)[0] == -1                  # y off the axis of a linear array
+    ura = np.zeros((4, 2))
+    ura[1, 1] = np.nan
+    r, h = call("ura", 2, 2, 2, 2, ura)
+    assert r == -1 and not h.value                                # not finite, rectangular array
+    assert call("ura", 2, 2, 128, 128, np.zeros((4, 2)))[0] == -4  # a 256 x 256 grid: beyond the 2-D kernel
